@@ -1,0 +1,225 @@
+/*
+ * shl.h -- C-ABI of libshl, periodic elastic homogenisation of
+ * charge-parametrised shells on NVIDIA B300 (sm_103a).
+ *
+ * Method: arXiv 2511.04025, "Shellular Metamaterial Design via Compact
+ * Electric Potential Parametrization".  The path is
+ *   charges -> truncated periodic potential F (Sec. 3.1, Eq. charge-field)
+ *   -> distance d = |F - c| / |grad F| at voxel centres and a shell of
+ *      half-thickness t (Sec. 4.1, Eq. beta)
+ *   -> six periodic cell problems K u^(k) = f^(k) on the voxel grid
+ *      (Eq. inv-design constraints; hex8 elements, K_e = E_e Khat)
+ *   -> C^H_ij = sum_e (chi^i + u^i_e)^T K_e (chi^j + u^j_e)  (Eq. inv-design)
+ *   -> dE/dtheta by the chain rule through the smoothed density (Eq. chain).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: r voxels per axis on the unit cell, h = 1/r.  Element and voxel
+ *     e = (iz*r + iy)*r + ix has its centre at ((ix+1/2)/r, ...); node
+ *     n = (iz*r + iy)*r + ix sits at (ix/r, iy/r, iz/r).  Everything is
+ *     periodic.
+ *   - Node vectors (displacements, loads) are structure-of-arrays: plane
+ *     p = 3*k + i holds component i of load case k, so element [p*N + n],
+ *     N = r^3.  A full set is 18 planes (6 load cases x 3 components).
+ *   - Voigt order 11, 22, 33, 23, 13, 12 with engineering shear strains;
+ *     C_out is 6x6 row-major.
+ *   - The cell problems are solved with node 0 pinned (its three DOFs
+ *     removed), which fixes the rigid translations; relres reports the
+ *     residual of that pinned system.
+ *   - Buffers ending in _dev are device pointers (a torch tensor's
+ *     data_ptr() is fine); every other pointer is host memory.  The caller
+ *     owns all of them; no call keeps a caller pointer after it returns
+ *     (serving requests are copied at submit).
+ *   - stream: a cudaStream_t passed as void*; NULL means the context's own
+ *     stream.  Calls that return results in host memory synchronise that
+ *     stream before returning; calls that only write _dev buffers do not.
+ *   - Every call returns an shl_status.  On failure shl_last_error() gives a
+ *     one-line reason.  Invalid arguments are rejected on the host before any
+ *     device work.
+ */
+#ifndef SHL_H
+#define SHL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SHL_OK = 0,
+    SHL_EINVAL = 1,    /* bad argument; nothing was launched                     */
+    SHL_ENOMEM = 2,    /* device workspace or admission budget exhausted         */
+    SHL_ENOCONV = 3,   /* max_iter reached; results and residuals still written  */
+    SHL_ENUMERIC = 4,  /* NaN/Inf met in a reduction                             */
+    SHL_ECUDA = 5,     /* a CUDA runtime call failed                             */
+    SHL_EAGAIN = 6,    /* serving: request not finished yet                      */
+    SHL_ENOTFOUND = 7  /* serving: unknown ticket                                */
+} shl_status;
+
+typedef enum { SHL_FP64 = 0, SHL_FP32_REFINE = 1 } shl_precision;
+typedef enum { SHL_MASK = 0, SHL_SMOOTH = 1 } shl_density;
+
+typedef struct shl_ctx shl_ctx;
+
+/* Context options.  device: CUDA ordinal.  max_batch: serving slots (designs
+ * in flight at once, 0 = 16).  hbm_budget_bytes: cap on device memory the
+ * serving scheduler may hold for in-flight designs (0 = 40 % of the device's
+ * free memory at creation). */
+typedef struct {
+    int32_t device;
+    int32_t max_batch;
+    uint64_t hbm_budget_bytes;
+} shl_opts;
+
+/*
+ * A charge design theta = {p_m, q_m, alpha_hkl} plus the shell (Sec. 3.1,
+ * Eq. charge-field):
+ *   F(p) = sum_{h,k,l=0..K} alpha_hkl w_hkl sum_j q_j
+ *          cos(2 pi h (x-x_j)) cos(2 pi k (y-y_j)) cos(2 pi l (z-z_j)) / (h^2+k^2+l^2)
+ * with w = 1, 1/2, 1/4 for none, one, two zero indices and B_000 = 0.
+ *   n      charges; pos n x 3 (any real, used mod 1); q n magnitudes
+ *   alpha  (K+1)^3 weights indexed [h][k][l], or NULL for all ones
+ *   K      truncation order, 1..7 (the paper uses 3)
+ *   iso    iso-level c: the shell is |F - c| <= t |grad F|
+ *   t      half-thickness in cell units if > 0; otherwise t is chosen so that
+ *          round(vf * r^3) voxels are solid (see shl_voxelize)
+ *   vf     target solid fraction in (0, 1) when t <= 0
+ */
+typedef struct {
+    int32_t n;
+    int32_t K;
+    const double *pos;
+    const double *q;
+    const double *alpha;
+    double iso;
+    double t;
+    double vf;
+} shl_design;
+
+/*
+ * Solver options (Eq. inv-design cell problems).
+ *   E, nu, E_void  solid modulus, Poisson ratio, ersatz void modulus; the
+ *                  element modulus is E_e = E_void + rho_e (E - E_void)
+ *   tol            stop each load case at ||f - K u||_2 / ||f||_2 <= tol
+ *                  (true FP64 residual of the pinned system)
+ *   max_iter       cap on CG iterations per load case, summed over restarts
+ *                  (FP64) or refinement steps (FP32_REFINE)
+ *   precision      SHL_FP64: PCG entirely in FP64, restarted from the true
+ *                  residual until it meets tol.
+ *                  SHL_FP32_REFINE: FP32 stiffness apply and vectors with
+ *                  FP64-class dot accumulation inside; outer FP64 residual
+ *                  f - K x and FP64 correction until tol.
+ *   density        SHL_MASK: binary rho; SHL_SMOOTH: rho = 1/(1+exp(-kappa(t-d)))
+ *   kappa          logistic sharpness; <= 0 selects ln(9) * r (two-voxel rise)
+ *   inner_tol      FP32_REFINE: relative reduction asked of each inner solve
+ *                  (<= 0 selects 1e-5)
+ *   warm_start     use the displacements passed in (shl_solve) or kept for the
+ *                  session (serving) as the initial guess
+ */
+typedef struct {
+    double E, nu, E_void;
+    double tol;
+    int32_t max_iter;
+    int32_t precision;
+    int32_t density;
+    int32_t warm_start;
+    double kappa;
+    double inner_tol;
+} shl_solve_opts;
+
+/* Per-result record. */
+typedef struct {
+    int32_t iters[6];      /* CG iterations per load case (summed over restarts)    */
+    double relres[6];      /* final ||f - K u|| / ||f|| per load case, FP64         */
+    int32_t n_refine;      /* restarts (FP64) or refinement steps (FP32_REFINE)    */
+    int32_t status;        /* shl_status of this result                            */
+    double t;              /* half-thickness used                                  */
+    double margin;         /* half gap around t when t was chosen from vf          */
+    int64_t n_solid;       /* voxels with d <= t                                   */
+    int64_t n_ambiguous;   /* voxels with |d - t| <= 1e-9 t                        */
+    float ms_field, ms_rhs, ms_solve, ms_chom; /* stage times (CUDA events)        */
+} shl_stats;
+
+int shl_create(const shl_opts *opts, shl_ctx **out);
+int shl_destroy(shl_ctx *ctx);
+const char *shl_last_error(shl_ctx *ctx);
+/* Default solver options: E=1, nu=0.3, E_void=1e-6, tol=1e-10, FP64, mask. */
+void shl_default_solve_opts(shl_solve_opts *o);
+
+/*
+ * F and grad F at the r^3 voxel centres (Sec. 3.1, Eq. charge-field and its
+ * analytic gradient), in FP64.  F_dev: r^3 doubles; gradF_dev: r^3 x 3
+ * doubles (x,y,z per voxel) or NULL.  2 <= r <= 1024.
+ */
+int shl_field(shl_ctx *ctx, const shl_design *d, int32_t r, double *F_dev, double *gradF_dev, void *stream);
+
+/*
+ * Voxelise the shell (Sec. 4.1, Eq. beta).  d_e = |F(p_e) - c| / |grad F(p_e)|
+ * (+inf where grad F = 0).  If d->t > 0 that t is used; otherwise t is chosen
+ * from d->vf: with d_(1) <= ... <= d_(n) sorted, k0 = round(vf n) clamped to
+ * [1, n-1], take the k nearest k0 (k0, k0-1, k0+1, ...; within 64 ranks) whose
+ * gap d_(k+1) - d_(k) exceeds 1e-9 d_(k+1), and t = (d_(k) + d_(k+1)) / 2.
+ *   mask_dev   r^3 bytes, 1 where d_e <= t (may be NULL)
+ *   rho_dev    r^3 doubles, the smoothed occupancy beta_e = 1/(1+exp(-kappa(t-d_e)))
+ *              (may be NULL); kappa <= 0 selects ln(9) r
+ *   d_dev      r^3 doubles receiving d_e (may be NULL)
+ *   t_out, margin_out, n_solid, n_ambiguous: host outputs (each may be NULL)
+ * Returns SHL_EINVAL when no resolvable gap lies within 64 ranks of k0.
+ */
+int shl_voxelize(shl_ctx *ctx, const shl_design *d, int32_t r, double kappa, uint8_t *mask_dev, double *rho_dev,
+                 double *d_dev, double *t_out, double *margin_out, int64_t *n_solid, int64_t *n_ambiguous,
+                 void *stream);
+
+/*
+ * q = K p, the assembled periodic stiffness K = sum_e E_e Khat applied
+ * matrix-free (Eq. inv-design; Sec. 4.2.2 computes finest-level stiffness on
+ * the fly).  nvec load cases (1..6) in the SoA layout above (3*nvec planes).
+ *   mask_dev   r^3 bytes: E_e = mask ? E : E_void   (used when rho_dev == NULL)
+ *   rho_dev    r^3 doubles: E_e = E_void + rho (E - E_void)
+ *   precision  SHL_FP64: p_dev, q_dev are double; SHL_FP32_REFINE: float
+ */
+int shl_apply(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+              double E_void, int32_t precision, int32_t nvec, const void *p_dev, void *q_dev, void *stream);
+
+/*
+ * Loads of the six cell problems, f^(k) = - sum_e K_e chi^k (Eq. inv-design),
+ * FP64, 18 SoA planes.  Density as in shl_apply.
+ */
+int shl_rhs(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+            double E_void, double *f_dev, void *stream);
+
+/*
+ * C^H_ij = sum_e E_e (chi^i + u^i_e)^T Khat (chi^j + u^j_e), |Y| = 1
+ * (Eq. inv-design), FP64 accumulation, from given displacements u_dev
+ * (18 SoA planes of doubles).  C_out: 36 host doubles.
+ */
+int shl_chom(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+             double E_void, const double *u_dev, double *C_out, void *stream);
+
+/*
+ * Solve the six periodic cell problems for a given density (node 0 pinned,
+ * Jacobi-preconditioned CG on all six load cases at once, per-case
+ * convergence and skip) and return C^H.  u_dev (18 SoA planes of doubles, may
+ * be NULL) receives the displacements; if o->warm_start it also supplies the
+ * initial guess.
+ */
+int shl_solve(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, const shl_solve_opts *o,
+              double *u_dev, double *C_out, shl_stats *st, void *stream);
+
+/*
+ * The whole path for one design: field, voxelisation (t from d->t or d->vf),
+ * the six cell problems and C^H.  C_out: 36 host doubles.  st may be NULL.
+ * Returns SHL_ENOCONV if a load case did not reach o->tol (C_out and st are
+ * still written).
+ */
+int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, double *C_out,
+                   shl_stats *st);
+
+/* n designs, each on its own r[i]^3 grid; C_out: n x 36; st: n records or NULL. */
+int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
+                         double *C_out, shl_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHL_H */

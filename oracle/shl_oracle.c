@@ -424,8 +424,8 @@ int shlo_rhs(int r, const double *rho, double E, double nu, double Evoid, double
  * removed: zero rows/columns, unit diagonal, zero load), by Jacobi-
  * preconditioned CG in FP64.  All six load cases share each SpMV; each has
  * its own CG scalars and stops once ||f - K u||_2 / ||f||_2 <= tol (the
- * recurrence residual).  relres returns the true residual of the unpinned
- * periodic system after the solve; iters the iterations each case used.
+ * recurrence residual).  relres returns the true residual of the pinned
+ * system after the solve; iters the iterations each case used.
  * Returns 0, or 3 if some case hit maxit.
  */
 int shlo_solve(int r, const double *rho, double E, double nu, double Evoid, double tol, int maxit, double *u,
@@ -507,11 +507,11 @@ int shlo_solve(int r, const double *rho, double E, double nu, double Evoid, doub
     int all = 1;
     for (int k = 0; k < 6; ++k) all &= done[k];
 
-    /* true residual of the unpinned system */
-    shlo_spmv(&A, 6, u, q);
+    /* true residual of the pinned system (the system CG solves) */
+    shlo_spmv(&P, 6, u, q);
     for (int k = 0; k < 6; ++k) {
-        for (long i = 0; i < L; ++i) q[k * L + i] = f[k * L + i] - q[k * L + i];
-        const double fnk = sqrt(shlo_dot(L, f + k * L, f + k * L));
+        for (long i = 0; i < L; ++i) q[k * L + i] = fp[k * L + i] - q[k * L + i];
+        const double fnk = sqrt(shlo_dot(L, fp + k * L, fp + k * L));
         const double rn = sqrt(shlo_dot(L, q + k * L, q + k * L));
         relres[k] = fnk > 0.0 ? rn / fnk : rn;
     }

@@ -1,0 +1,230 @@
+// common.cuh -- shared definitions of libshl (context, errors, workspaces,
+// reductions).  Everything in csrc/ is compiled as one translation unit
+// (shl.cu) for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/shl.h"
+
+namespace shl {
+
+constexpr int kBlk = 256;
+
+// Last error text is per context; calls made without a context (argument
+// errors before creation) write to a process-wide buffer.
+struct ErrState {
+    std::string msg;
+};
+
+inline ErrState &global_err() {
+    static ErrState e;
+    return e;
+}
+
+}  // namespace shl
+
+// Device workspace cache: named slots of device memory reused across calls
+// (re-allocated only when a call needs more bytes than the slot holds).
+struct shl_workspace {
+    std::map<std::string, std::pair<void *, size_t>> slots;
+};
+
+struct shl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    shl_opts opts{};
+    std::string err;
+    shl_workspace ws;
+    std::recursive_mutex mu;  // serialises public calls on one context
+    void *serve = nullptr;    // serving scheduler state (serve.cuh)
+};
+
+namespace shl {
+
+inline int set_err(shl_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        global_err().msg = buf;
+    return code;
+}
+
+#define SHL_CUDA(ctx, call)                                                                            \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return shl::set_err((ctx), SHL_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                __FILE__, __LINE__);                                                   \
+    } while (0)
+
+#define SHL_TRY(x)                   \
+    do {                             \
+        int s_ = (x);                \
+        if (s_ != SHL_OK) return s_; \
+    } while (0)
+
+// Get (allocating or growing) a named device workspace slot.  Fresh slots are
+// zero-filled (reduction tickets rely on it).
+inline int ws_get(shl_ctx *ctx, const std::string &name, size_t bytes, void **out) {
+    auto &slot = ctx->ws.slots[name];
+    if (slot.second < bytes) {
+        if (slot.first) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(slot.first);
+        }
+        slot.first = nullptr;
+        slot.second = 0;
+        size_t sz = bytes < 256 ? 256 : bytes;
+        cudaError_t e = cudaMalloc(&slot.first, sz);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, SHL_ENOMEM, "cudaMalloc(%zu) for workspace '%s' failed: %s", sz, name.c_str(),
+                           cudaGetErrorString(e));
+        }
+        slot.second = sz;
+        e = cudaMemset(slot.first, 0, sz);
+        if (e != cudaSuccess) return set_err(ctx, SHL_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+    }
+    *out = slot.first;
+    return SHL_OK;
+}
+
+template <typename T>
+inline int ws_get_t(shl_ctx *ctx, const std::string &name, size_t count, T **out) {
+    void *p = nullptr;
+    int s = ws_get(ctx, name, count * sizeof(T), &p);
+    *out = static_cast<T *>(p);
+    return s;
+}
+
+inline void ws_free_all(shl_ctx *ctx) {
+    for (auto &kv : ctx->ws.slots)
+        if (kv.second.first) cudaFree(kv.second.first);
+    ctx->ws.slots.clear();
+}
+
+inline cudaStream_t pick_stream(shl_ctx *ctx, void *s) { return s ? static_cast<cudaStream_t>(s) : ctx->stream; }
+
+__host__ __device__ inline int wrapi(int v, int r) {
+    v %= r;
+    return v < 0 ? v + r : v;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic grid reductions: every block writes its partial sums to
+// partial[block*NV + v]; the last block to finish (ticket counter) combines
+// the partials in a fixed order.  Bitwise reproducible for a fixed launch
+// shape.  Blocks must be a multiple of 32 threads.
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ inline void block_reduce_store(double (&v)[NV], double *partial, int block_id) {
+    __shared__ double red[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[k][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[threadIdx.x][w];
+        partial[(size_t)block_id * NV + threadIdx.x] = s;
+    }
+}
+
+// Per-thread dot-product accumulator.  FP64 vectors accumulate in FP64.  FP32
+// vectors accumulate each thread's few products with compensated (Kahan)
+// FP32 summation and hand the result to the FP64 block/grid reduction: the
+// per-element work stays on the FP32 pipes (B300 has a very low FP64 rate)
+// while the accumulated sum keeps FP64-class accuracy.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// Returns true in every thread of the block that finished last.  Resets the
+// ticket for the next launch.
+__device__ inline bool last_block_ticket(unsigned *ticket, unsigned nblocks) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == nblocks - 1);
+        if (is_last) *ticket = 0;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// Sum partial[b*NV + v] over blocks (run by the last block).  Thread t adds
+// blocks t, t+blockDim, ... in order, then a fixed shuffle/shared-memory
+// tree combines the threads: the result depends only on the launch shape.
+// out[v] is written by thread 0 and visible to the whole block on return.
+template <int NV>
+__device__ inline void sum_partials_ordered(const double *partial, unsigned nblocks, double *out) {
+    __shared__ double red[NV][32];
+    double s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] += __ldcg(partial + (size_t)b * NV + v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double x = s[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[v][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < NV; ++v) {
+            double x = 0.0;
+            for (int w = 0; w < nwarps; ++w) x += red[v][w];
+            out[v] = x;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace shl

@@ -1,0 +1,194 @@
+// pcg.cuh -- batched 6-RHS Jacobi-preconditioned conjugate gradients with
+// device-resident scalars, per-load-case convergence and skip (Sec. 4.2.2:
+// all six right-hand sides in the same kernels, per-RHS residual tracking,
+// converged RHS skip their updates), plus the precision-refinement helpers.
+#pragma once
+
+#include "apply.cuh"
+
+namespace shl {
+
+template <typename T>
+struct VecArgs {
+    size_t N;
+    T *x, *r, *p;
+    const T *q;
+    const T *dinv;
+    PcgState *st;
+    double *partial;
+};
+
+// x += alpha p ; r -= alpha q ; z = D^-1 r ; partial (r.z, r.r)
+// Last block: convergence test, beta, active flags.
+template <typename T>
+__global__ void pcg_update_kernel(VecArgs<T> a) {
+    PcgState *st = a.st;
+    if (st->nactive == 0) return;
+    bool act[6];
+    T al[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        act[k] = st->active[k] != 0;
+        al[k] = (T)st->alpha[k];
+    }
+    DotAcc<T> dacc[12];
+    const size_t N = a.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const T di = a.dinv[n];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!act[k]) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                const T pv = a.p[o], qv = a.q[o];
+                a.x[o] += al[k] * pv;
+                const T rv = a.r[o] - al[k] * qv;
+                a.r[o] = rv;
+                dacc[k].add(rv * (di * rv));
+                dacc[6 + k].add(rv * rv);
+            }
+        }
+    }
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = dacc[k].get();
+    const unsigned nb = gridDim.x;
+    block_reduce_store<12>(acc, a.partial, blockIdx.x);
+    if (!last_block_ticket(&st->ticket_update, nb)) return;
+    __shared__ double tot[12];
+    sum_partials_ordered<12>(a.partial, nb, tot);
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int k = 0; k < 6; ++k) {
+            if (!act[k]) continue;
+            st->iters[k] += 1;
+            const double rz = tot[k], rr = tot[6 + k];
+            st->rr[k] = rr;
+            if (!isfinite(rz) || !isfinite(rr)) {
+                st->numeric_err = 1;
+                st->active[k] = 0;
+            } else if (rr <= st->tol2 * st->bnorm2[k]) {
+                st->active[k] = 0;
+            } else if (st->iters[k] >= st->maxit) {
+                st->active[k] = 0;
+            } else {
+                st->beta[k] = rz / st->rz[k];
+                st->rz[k] = rz;
+            }
+        }
+        for (int k = 0; k < 6; ++k) na += st->active[k];
+        st->nactive = na;
+    }
+}
+
+// p = D^-1 r + beta p
+template <typename T>
+__global__ void pcg_direction_kernel(VecArgs<T> a) {
+    PcgState *st = a.st;
+    if (st->nactive == 0) return;
+    bool act[6];
+    T be[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        act[k] = st->active[k] != 0;
+        be[k] = (T)st->beta[k];
+    }
+    const size_t N = a.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const T di = a.dinv[n];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!act[k]) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                a.p[o] = di * a.r[o] + be[k] * a.p[o];
+            }
+        }
+    }
+}
+
+// Start of a solve: p = z = D^-1 r, rz = r.z, rr = r.r, active = rr > tol2 bnorm2.
+// want_mask selects the load cases to solve (others stay inactive).
+template <typename T>
+__global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
+    PcgState *st = a.st;
+    DotAcc<T> dacc[12];
+    const size_t N = a.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const T di = a.dinv[n];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!((want_mask >> k) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                const T rv = a.r[o];
+                const T z = di * rv;
+                a.p[o] = z;
+                dacc[k].add(rv * z);
+                dacc[6 + k].add(rv * rv);
+            }
+        }
+    }
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = dacc[k].get();
+    const unsigned nb = gridDim.x;
+    block_reduce_store<12>(acc, a.partial, blockIdx.x);
+    if (!last_block_ticket(&st->ticket_aux, nb)) return;
+    __shared__ double tot[12];
+    sum_partials_ordered<12>(a.partial, nb, tot);
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int k = 0; k < 6; ++k) {
+            st->iters[k] = 0;
+            st->alpha[k] = st->beta[k] = 0.0;
+            st->rz[k] = tot[k];
+            st->rr[k] = tot[6 + k];
+            if (set_bnorm) st->bnorm2[k] = tot[6 + k];
+            const bool want = (want_mask >> k) & 1;
+            st->active[k] = want && (tot[6 + k] > st->tol2 * st->bnorm2[k]) && st->bnorm2[k] > 0.0;
+            if (want && !isfinite(tot[6 + k])) {
+                st->numeric_err = 1;
+                st->active[k] = 0;
+            }
+            na += st->active[k];
+        }
+        st->nactive = na;
+    }
+}
+
+// ---- refinement helpers ----------------------------------------------------
+
+// b32 = r64 / s_k for the load cases in mask (s_k = ||r64_k||), x32 = 0.
+__global__ void refine_scatter_kernel(size_t N, const double *r64, const double *scale, int mask, float *b32,
+                                      float *x32) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 6; ++k) {
+            if (!((mask >> k) & 1)) continue;
+            const double inv = 1.0 / scale[k];
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                b32[o] = (float)(r64[o] * inv);
+                x32[o] = 0.0f;
+            }
+        }
+    }
+}
+
+// x64 += s_k x32
+__global__ void refine_gather_kernel(size_t N, const float *x32, const double *scale, int mask, double *x64) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 6; ++k) {
+            if (!((mask >> k) & 1)) continue;
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                x64[o] += scale[k] * (double)x32[o];
+            }
+        }
+    }
+}
+
+}  // namespace shl

@@ -1,0 +1,730 @@
+// shl.cu -- libshl C-ABI entry points (include/shl.h) and the host drivers of
+// the solve.  One translation unit for the whole library.
+#include "chom.cuh"
+#include "common.cuh"
+#include "element.cuh"
+#include "field.cuh"
+#include "pcg.cuh"
+
+using namespace shl;
+
+namespace shl {
+
+constexpr int kTX = 16, kTY = 16;
+using Shape = ApplyShape<kTX, kTY>;
+
+inline int grid1d(size_t n, int threads = kBlk, int cap = 148 * 8) {
+    size_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (size_t)cap) b = cap;
+    return (int)b;
+}
+
+template <typename T>
+void apply_smem_attr() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(apply_kernel<T, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Shape::smem<T>());
+        done = true;
+    }
+}
+
+// z-extent of a CTA's tile: long enough to amortise the halo plane, short
+// enough to give two CTAs per SM at the grid sizes in use.
+inline int pick_tz(int r) {
+    const int nxy = ((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY);
+    int tz = 16;
+    while (tz > 4 && (size_t)nxy * ((r + tz - 1) / tz) < 2 * 148) tz >>= 1;
+    return tz;
+}
+
+inline dim3 apply_grid(int r, int tz) { return dim3((r + kTX - 1) / kTX, (r + kTY - 1) / kTY, (r + tz - 1) / tz); }
+
+template <typename T>
+int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
+    apply_smem_attr<T>();
+    a.tz = pick_tz(a.r);
+    const dim3 g = apply_grid(a.r, a.tz);
+    if (a.dot) {
+        if (!a.partial) {
+            double *partial = nullptr;
+            SHL_TRY(ws_get_t(ctx, "apply_partial", (size_t)g.x * g.y * g.z * 6, &partial));
+            a.partial = partial;
+        }
+        if (!a.ticket) {
+            unsigned *ticket = nullptr;
+            SHL_TRY(ws_get_t(ctx, "apply_ticket", 1, &ticket));
+            a.ticket = ticket;
+        }
+    }
+    apply_kernel<T, kTX, kTY><<<g, Shape::THREADS, Shape::smem<T>(), s>>>(a);
+    SHL_CUDA(ctx, cudaGetLastError());
+    return SHL_OK;
+}
+
+template <typename T>
+int get_op(shl_ctx *ctx, double nu, int r, ElemOp<T> *op) {
+    const double off = build_elem_op<T>(nu, r, op);
+    if (!(off < 1e-12)) return set_err(ctx, SHL_EINVAL, "element operator is not block diagonal (%g)", off);
+    return SHL_OK;
+}
+
+struct Uploaded {
+    double *pos, *q, *alpha;
+};
+
+inline int validate_design(shl_ctx *ctx, const shl_design *d, int r) {
+    if (!d) return set_err(ctx, SHL_EINVAL, "design is NULL");
+    if (d->n < 1 || d->n > (1 << 20)) return set_err(ctx, SHL_EINVAL, "charge count %d out of range [1, 2^20]", d->n);
+    if (d->K < 1 || d->K > kMaxK)
+        return set_err(ctx, SHL_EINVAL, "truncation order K=%d out of range [1, %d]", d->K, kMaxK);
+    if (!d->pos || !d->q) return set_err(ctx, SHL_EINVAL, "design pos/q is NULL");
+    if (r < 2 || r > 1024) return set_err(ctx, SHL_EINVAL, "grid size r=%d out of range [2, 1024]", r);
+    for (int j = 0; j < 3 * d->n; ++j)
+        if (!std::isfinite(d->pos[j])) return set_err(ctx, SHL_EINVAL, "non-finite charge position");
+    for (int j = 0; j < d->n; ++j)
+        if (!std::isfinite(d->q[j])) return set_err(ctx, SHL_EINVAL, "non-finite charge magnitude");
+    if (!std::isfinite(d->iso)) return set_err(ctx, SHL_EINVAL, "non-finite iso-level");
+    if (!(d->t > 0.0) && !(d->vf > 0.0 && d->vf < 1.0))
+        return set_err(ctx, SHL_EINVAL, "design needs t > 0 or a volume fraction in (0,1), got t=%g vf=%g", d->t,
+                       d->vf);
+    return SHL_OK;
+}
+
+inline int upload_design(shl_ctx *ctx, const shl_design *d, cudaStream_t s, Uploaded *u, const char *tag) {
+    const int na = (d->K + 1) * (d->K + 1) * (d->K + 1);
+    double *buf = nullptr;
+    SHL_TRY(ws_get_t(ctx, std::string("design_") + tag, (size_t)4 * d->n + na, &buf));
+    u->pos = buf;
+    u->q = buf + 3 * d->n;
+    u->alpha = d->alpha ? buf + 4 * d->n : nullptr;
+    SHL_CUDA(ctx, cudaMemcpyAsync(u->pos, d->pos, sizeof(double) * 3 * d->n, cudaMemcpyHostToDevice, s));
+    SHL_CUDA(ctx, cudaMemcpyAsync(u->q, d->q, sizeof(double) * d->n, cudaMemcpyHostToDevice, s));
+    if (d->alpha) SHL_CUDA(ctx, cudaMemcpyAsync(u->alpha, d->alpha, sizeof(double) * na, cudaMemcpyHostToDevice, s));
+    return SHL_OK;
+}
+
+// F / gradF / d on the grid.
+inline int run_field(shl_ctx *ctx, const shl_design *d, int r, double *F, double *gF, double *dd, cudaStream_t s) {
+    Uploaded u;
+    SHL_TRY(upload_design(ctx, d, s, &u, "field"));
+    const int nb = 2 * d->K + 1;
+    double *A = nullptr;
+    SHL_TRY(ws_get_t(ctx, "field_A", (size_t)nb * nb * nb, &A));
+    field_coef_kernel<<<1, 512, 0, s>>>(d->n, d->K, u.pos, u.q, u.alpha, A);
+    SHL_CUDA(ctx, cudaGetLastError());
+    int lines = r;
+    while (lines > 1 && field_smem_bytes(r, d->K, lines) > 96 * 1024) lines = (lines + 1) / 2;
+    while (lines > 4 && (size_t)r * ((r + lines - 1) / lines) < 4 * 148) lines = (lines + 1) / 2;
+    FieldArgs fa{r, d->K, lines, d->iso, A, F, gF, dd};
+    const size_t smem = field_smem_bytes(r, d->K, lines);
+    cudaFuncSetAttribute(field_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    field_grid_kernel<<<dim3(r, (r + lines - 1) / lines), 256, smem, s>>>(fa);
+    SHL_CUDA(ctx, cudaGetLastError());
+    return SHL_OK;
+}
+
+// Threshold selection from d (device); result left in the device SelectState.
+inline int run_select(shl_ctx *ctx, const double *dd, size_t n, double vf, cudaStream_t s, SelectState **out) {
+    SelectState *st = nullptr;
+    SHL_TRY(ws_get_t(ctx, "select_state", 1, &st));
+    long long k0 = llround(vf * (double)n);
+    if (k0 < 1) k0 = 1;
+    if (k0 > (long long)n - 1) k0 = (long long)n - 1;
+    const long long lo = std::max(1LL, k0 - kSelW), hi = std::min((long long)n, k0 + kSelW + 1);
+    static SelectState init;  // host staging (only the header part is copied)
+    std::memset(&init, 0, offsetof(SelectState, buf));
+    init.rank[0] = (unsigned long long)lo;
+    init.rank[1] = (unsigned long long)hi;
+    SHL_CUDA(ctx, cudaMemcpyAsync(st, &init, offsetof(SelectState, buf), cudaMemcpyHostToDevice, s));
+    const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(dd);
+    const int g = grid1d(n, 256, 148 * 4);
+    const int shifts[6] = {53, 42, 31, 20, 9, 0};
+    const int widths[6] = {11, 11, 11, 11, 11, 9};
+    for (int p = 0; p < 6; ++p) {
+        select_hist_kernel<<<g, 256, 0, s>>>(keys, n, st, shifts[p], widths[p]);
+        select_choose_kernel<<<1, 256, 0, s>>>(st, shifts[p]);
+    }
+    select_gather_kernel<<<g, 256, 0, s>>>(keys, n, st);
+    select_finish_kernel<<<1, 1024, 0, s>>>(st, (long long)n, k0);
+    SHL_CUDA(ctx, cudaGetLastError());
+    // the host staging struct is reused: make sure its copy has completed
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    *out = st;
+    return SHL_OK;
+}
+
+struct VoxOut {
+    double t = 0, margin = 0;
+    long long n_solid = 0, n_amb = 0;
+};
+
+inline int run_voxelize(shl_ctx *ctx, const shl_design *d, int r, double kappa, uint8_t *mask, double *rho,
+                        double *d_out, cudaStream_t s, VoxOut *res) {
+    const size_t n = (size_t)r * r * r;
+    const bool choose = !(d->t > 0.0);
+    double *dd = d_out;
+    if (!dd) SHL_TRY(ws_get_t(ctx, "vox_d", n, &dd));
+    SHL_TRY(run_field(ctx, d, r, nullptr, nullptr, dd, s));
+    SelectState *sel = nullptr;
+    if (choose) SHL_TRY(run_select(ctx, dd, n, d->vf, s, &sel));
+    unsigned long long *counts = nullptr;
+    SHL_TRY(ws_get_t(ctx, "vox_counts", 2, &counts));
+    SHL_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
+    if (kappa <= 0.0) kappa = std::log(9.0) * r;
+    voxel_mask_kernel<<<grid1d(n, 256, 148 * 8), 256, 0, s>>>(dd, n, sel, d->t, kappa, mask, rho, counts);
+    SHL_CUDA(ctx, cudaGetLastError());
+    unsigned long long hc[2];
+    SHL_CUDA(ctx, cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    if (choose) {
+        int status = 0;
+        double t = 0, margin = 0;
+        SHL_CUDA(ctx, cudaMemcpyAsync(&status, &sel->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SHL_CUDA(ctx, cudaMemcpyAsync(&t, &sel->t, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SHL_CUDA(ctx, cudaMemcpyAsync(&margin, &sel->margin, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SHL_CUDA(ctx, cudaStreamSynchronize(s));
+        if (status == 2) return set_err(ctx, SHL_EINVAL, "threshold selection: too many tied distances near rank");
+        if (status != 0) return set_err(ctx, SHL_EINVAL, "threshold selection: no resolvable gap within 64 ranks");
+        res->t = t;
+        res->margin = margin;
+    } else {
+        SHL_CUDA(ctx, cudaStreamSynchronize(s));
+        res->t = d->t;
+        res->margin = 0.0;
+    }
+    res->n_solid = (long long)hc[0];
+    res->n_amb = (long long)hc[1];
+    return SHL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solver
+// ---------------------------------------------------------------------------
+
+__global__ void pcg_config_kernel(PcgState *st, double tol2, int maxit, int reset) {
+    if (threadIdx.x == 0) {
+        if (reset) {
+            for (int k = 0; k < 6; ++k) {
+                st->rz[k] = st->alpha[k] = st->beta[k] = st->rr[k] = st->bnorm2[k] = 0.0;
+                st->active[k] = 0;
+                st->iters[k] = 0;
+            }
+            st->nactive = 0;
+            st->numeric_err = 0;
+            st->ticket_apply = st->ticket_update = st->ticket_aux = 0;
+        }
+        st->tol2 = tol2;
+        st->maxit = maxit;
+    }
+}
+
+template <typename T>
+struct Bufs {
+    T *x, *r, *p, *q, *dinv;
+};
+
+struct Density {
+    const uint8_t *mask;
+    const double *rho;
+    double E, Ev;
+};
+
+template <typename T>
+ApplyArgs<T> make_apply(int r, const Density &den, const ElemOp<T> &op) {
+    ApplyArgs<T> a{};
+    a.r = r;
+    a.N = (size_t)r * r * r;
+    a.nvec = 6;
+    a.mask = den.mask;
+    a.rho = den.rho;
+    a.E = (T)den.E;
+    a.Evoid = (T)den.Ev;
+    a.op = op;
+    return a;
+}
+
+// Runs PCG from the residual in b.r and the iterate in b.x for the load cases
+// in want.  The device deactivates each case at convergence or st->maxit; the
+// host polls the active count every chunk of iterations.
+template <typename T>
+int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T> &b, PcgState *st, int want,
+            int set_bnorm, cudaStream_t s, int *host_nactive, int max_iters_backstop) {
+    const size_t N = (size_t)r * r * r;
+    double *partial = nullptr;
+    const int gv = grid1d(N, kBlk, 148 * 4);
+    SHL_TRY(ws_get_t(ctx, "pcg_partial", (size_t)gv * 12, &partial));
+    VecArgs<T> va{N, b.x, b.r, b.p, b.q, b.dinv, st, partial};
+    pcg_init_kernel<T><<<gv, kBlk, 0, s>>>(va, want, set_bnorm);
+    SHL_CUDA(ctx, cudaGetLastError());
+    ApplyArgs<T> a = make_apply<T>(r, den, op);
+    a.p = b.p;
+    a.q = b.q;
+    a.pin = 1;
+    a.dot = 1;
+    a.st = st;
+    a.ticket = &st->ticket_apply;
+    const int chunk = 32;
+    const long long cap = (long long)max_iters_backstop + 2 * chunk;
+    for (long long it = 0;; it += chunk) {
+        if (it > cap) return set_err(ctx, SHL_ENOCONV, "PCG did not stop within %lld iterations", cap);
+        for (int c = 0; c < chunk; ++c) {
+            SHL_TRY(launch_apply<T>(ctx, a, s));
+            pcg_update_kernel<T><<<gv, kBlk, 0, s>>>(va);
+            pcg_direction_kernel<T><<<gv, kBlk, 0, s>>>(va);
+        }
+        SHL_CUDA(ctx, cudaGetLastError());
+        SHL_CUDA(ctx, cudaMemcpyAsync(host_nactive, &st->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SHL_CUDA(ctx, cudaStreamSynchronize(s));
+        if (*host_nactive == 0) break;
+    }
+    return SHL_OK;
+}
+
+struct SolveOut {
+    int iters[6] = {0, 0, 0, 0, 0, 0};
+    double relres[6] = {0, 0, 0, 0, 0, 0};
+    int n_refine = 0;
+    int status = SHL_OK;
+};
+
+// Residual f - K x (FP64) with its squared norms per load case; pin selects
+// the pinned system.
+inline int resid64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double> &op, const double *x, double *out,
+                   int pin, double *dot_out, cudaStream_t s) {
+    ApplyArgs<double> a = make_apply<double>(r, den, op);
+    a.p = x;
+    a.q = out;
+    a.pin = pin;
+    a.resid = 1;
+    a.dot = 2;
+    a.dot_out = dot_out;
+    return launch_apply<double>(ctx, a, s);
+}
+
+struct HostPinned {
+    int *nactive = nullptr;
+    double *v = nullptr;  // 64 doubles
+};
+
+inline int host_pinned(shl_ctx *ctx, HostPinned *hp) {
+    static thread_local HostPinned cache;
+    if (!cache.nactive) {
+        SHL_CUDA(ctx, cudaMallocHost(&cache.nactive, sizeof(int) * 4));
+        SHL_CUDA(ctx, cudaMallocHost(&cache.v, sizeof(double) * 64));
+    }
+    *hp = cache;
+    return SHL_OK;
+}
+
+// Full solve: x64 (18 N doubles, device) receives the displacements.
+inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_opts *o, double *x64, bool warm,
+                     cudaStream_t s, SolveOut *out) {
+    const size_t N = (size_t)r * r * r;
+    const size_t NV = 18 * N;
+    HostPinned hp;
+    SHL_TRY(host_pinned(ctx, &hp));
+    ElemOp<double> op64;
+    SHL_TRY(get_op(ctx, o->nu, r, &op64));
+    double *r64 = nullptr, *norms = nullptr;
+    SHL_TRY(ws_get_t(ctx, "r64", NV, &r64));
+    SHL_TRY(ws_get_t(ctx, "norms", 32, &norms));  // [0:6] |f|^2, [12:18] |f - K x|^2 (pinned system)
+    double *zero = nullptr;
+    SHL_TRY(ws_get_t(ctx, "zero64", NV, &zero));
+    SHL_CUDA(ctx, cudaMemsetAsync(zero, 0, NV * sizeof(double), s));
+    if (!warm) SHL_CUDA(ctx, cudaMemsetAsync(x64, 0, NV * sizeof(double), s));
+    // ||f||^2 of the pinned system (r64 = f afterwards)
+    SHL_TRY(resid64(ctx, r, den, op64, zero, r64, 1, norms + 0, s));
+    double fpin[6];
+    SHL_CUDA(ctx, cudaMemcpyAsync(fpin, norms, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    const double tol = o->tol;
+    const int maxit = o->max_iter > 0 ? o->max_iter : 100000;
+    int total_it[6] = {0, 0, 0, 0, 0, 0};
+    if (o->precision == SHL_FP64) {
+        Bufs<double> b{x64, r64, nullptr, nullptr, nullptr};
+        SHL_TRY(ws_get_t(ctx, "p64", NV, &b.p));
+        SHL_TRY(ws_get_t(ctx, "q64", NV, &b.q));
+        SHL_TRY(ws_get_t(ctx, "dinv64", N, &b.dinv));
+        dinv_kernel<double><<<grid1d(N), kBlk, 0, s>>>(r, den.mask, den.rho, den.E, den.Ev, op64.diag, b.dinv);
+        PcgState *st = nullptr;
+        SHL_TRY(ws_get_t(ctx, "pcg_state64", 1, &st));
+        pcg_config_kernel<<<1, 32, 0, s>>>(st, tol * tol, maxit, 1);
+        SHL_CUDA(ctx, cudaMemcpyAsync(st->bnorm2, norms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (warm) SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, nullptr, s));
+        // CG stops on its recurrence residual, which drifts from f - K x in
+        // finite precision; restart from the true residual until it meets tol.
+        int want = 0x3f, restarts = 0;
+        for (;; ++restarts) {
+            SHL_TRY(pcg_run<double>(ctx, r, den, op64, b, st, want, 0, s, hp.nactive, maxit));
+            int its[6], nerr = 0;
+            SHL_CUDA(ctx, cudaMemcpyAsync(its, st->iters, sizeof(its), cudaMemcpyDeviceToHost, s));
+            SHL_CUDA(ctx, cudaMemcpyAsync(&nerr, &st->numeric_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+            SHL_CUDA(ctx, cudaMemcpyAsync(hp.v, norms + 12, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SHL_CUDA(ctx, cudaStreamSynchronize(s));
+            for (int k = 0; k < 6; ++k)
+                if ((want >> k) & 1) total_it[k] += its[k];
+            if (nerr) {
+                out->status = SHL_ENUMERIC;
+                break;
+            }
+            want = 0;
+            for (int k = 0; k < 6; ++k)
+                if (fpin[k] > 0.0 && hp.v[k] > tol * tol * fpin[k] && total_it[k] < maxit) want |= 1 << k;
+            if (!want || restarts >= 20) break;
+        }
+        out->n_refine = restarts;
+    } else if (o->precision == SHL_FP32_REFINE) {
+        ElemOp<float> op32;
+        SHL_TRY(get_op(ctx, o->nu, r, &op32));
+        Bufs<float> b{};
+        SHL_TRY(ws_get_t(ctx, "x32", NV, &b.x));
+        SHL_TRY(ws_get_t(ctx, "r32", NV, &b.r));
+        SHL_TRY(ws_get_t(ctx, "p32", NV, &b.p));
+        SHL_TRY(ws_get_t(ctx, "q32", NV, &b.q));
+        SHL_TRY(ws_get_t(ctx, "dinv32", N, &b.dinv));
+        dinv_kernel<float><<<grid1d(N), kBlk, 0, s>>>(r, den.mask, den.rho, den.E, den.Ev, op64.diag, b.dinv);
+        PcgState *st = nullptr;
+        SHL_TRY(ws_get_t(ctx, "pcg_state32", 1, &st));
+        double *scale = nullptr;
+        SHL_TRY(ws_get_t(ctx, "refine_scale", 8, &scale));
+        const double itol = o->inner_tol > 0.0 ? o->inner_tol : 1e-5;
+        const int max_outer = 40;
+        int outer = 0;
+        for (;; ++outer) {
+            SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+            SHL_CUDA(ctx, cudaMemcpyAsync(hp.v, norms + 12, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SHL_CUDA(ctx, cudaStreamSynchronize(s));
+            int want = 0;
+            double sc[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+            for (int k = 0; k < 6; ++k) {
+                if (!std::isfinite(hp.v[k])) {
+                    out->status = SHL_ENUMERIC;
+                    continue;
+                }
+                if (fpin[k] > 0.0 && hp.v[k] > tol * tol * fpin[k] && total_it[k] < maxit) {
+                    want |= 1 << k;
+                    sc[k] = std::sqrt(hp.v[k]);
+                }
+            }
+            if (!want || outer >= max_outer || out->status == SHL_ENUMERIC) break;
+            SHL_CUDA(ctx, cudaMemcpyAsync(scale, sc, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
+            refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, scale, want, b.r, b.x);
+            pcg_config_kernel<<<1, 32, 0, s>>>(st, itol * itol, maxit, 1);
+            SHL_TRY(pcg_run<float>(ctx, r, den, op32, b, st, want, 1, s, hp.nactive, maxit));
+            refine_gather_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, scale, want, x64);
+            int its[6], nerr = 0;
+            SHL_CUDA(ctx, cudaMemcpyAsync(its, st->iters, sizeof(its), cudaMemcpyDeviceToHost, s));
+            SHL_CUDA(ctx, cudaMemcpyAsync(&nerr, &st->numeric_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SHL_CUDA(ctx, cudaStreamSynchronize(s));
+            if (nerr) out->status = SHL_ENUMERIC;
+            for (int k = 0; k < 6; ++k)
+                if ((want >> k) & 1) total_it[k] += its[k];
+        }
+        out->n_refine = outer;
+    } else {
+        return set_err(ctx, SHL_EINVAL, "unknown precision mode %d", o->precision);
+    }
+    for (int k = 0; k < 6; ++k) out->iters[k] = total_it[k];
+    // true residual of the pinned system, FP64
+    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+    double hn[24];
+    SHL_CUDA(ctx, cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int k = 0; k < 6; ++k) {
+        out->relres[k] = hn[k] > 0.0 ? std::sqrt(hn[12 + k] / hn[k]) : std::sqrt(hn[12 + k]);
+        if (!std::isfinite(out->relres[k]))
+            out->status = SHL_ENUMERIC;
+        else if (out->status == SHL_OK && out->relres[k] > tol)
+            out->status = SHL_ENOCONV;
+    }
+    return SHL_OK;
+}
+
+inline int run_chom(shl_ctx *ctx, int r, const Density &den, double nu, const double *u, double *C_dev,
+                    cudaStream_t s) {
+    ElemOp<double> op;
+    SHL_TRY(get_op(ctx, nu, r, &op));
+    const size_t N = (size_t)r * r * r;
+    const int g = grid1d(N, kChomThreads, 148 * 8);
+    double *partial = nullptr;
+    unsigned *ticket = nullptr;
+    SHL_TRY(ws_get_t(ctx, "chom_partial", (size_t)g * 21, &partial));
+    SHL_TRY(ws_get_t(ctx, "chom_ticket", 1, &ticket));
+    ChomArgs a{};
+    a.r = r;
+    a.N = N;
+    a.u = u;
+    a.mask = den.mask;
+    a.rho = den.rho;
+    a.E = den.E;
+    a.Evoid = den.Ev;
+    a.partial = partial;
+    a.ticket = ticket;
+    a.C = C_dev;
+    a.op = op;
+    const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
+    cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    chom_kernel<<<g, kChomThreads, smem, s>>>(a);
+    SHL_CUDA(ctx, cudaGetLastError());
+    return SHL_OK;
+}
+
+inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
+    if (!o) return set_err(ctx, SHL_EINVAL, "solve options are NULL");
+    if (!(o->E > 0.0) || !(o->E_void >= 0.0) || !(o->E_void < o->E))
+        return set_err(ctx, SHL_EINVAL, "moduli must satisfy 0 <= E_void < E");
+    if (!(o->nu > -1.0 && o->nu < 0.5)) return set_err(ctx, SHL_EINVAL, "Poisson ratio %g outside (-1, 0.5)", o->nu);
+    if (!(o->tol > 0.0 && o->tol < 1.0)) return set_err(ctx, SHL_EINVAL, "tol %g outside (0, 1)", o->tol);
+    if (o->precision != SHL_FP64 && o->precision != SHL_FP32_REFINE)
+        return set_err(ctx, SHL_EINVAL, "unknown precision %d", o->precision);
+    if (o->density != SHL_MASK && o->density != SHL_SMOOTH)
+        return set_err(ctx, SHL_EINVAL, "unknown density mode %d", o->density);
+    return SHL_OK;
+}
+
+}  // namespace shl
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+void shl_default_solve_opts(shl_solve_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->E = 1.0;
+    o->nu = 0.3;
+    o->E_void = 1e-6;
+    o->tol = 1e-10;
+    o->max_iter = 100000;
+    o->precision = SHL_FP64;
+    o->density = SHL_MASK;
+    o->kappa = 0.0;
+    o->inner_tol = 1e-5;
+}
+
+int shl_create(const shl_opts *opts, shl_ctx **out) {
+    if (!out) return set_err(nullptr, SHL_EINVAL, "out is NULL");
+    *out = nullptr;
+    int dev = opts ? opts->device : 0;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_err(nullptr, SHL_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= ndev) return set_err(nullptr, SHL_EINVAL, "device %d out of range", dev);
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return set_err(nullptr, SHL_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    shl_ctx *c = new shl_ctx();
+    c->device = dev;
+    if (opts) c->opts = *opts;
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return set_err(nullptr, SHL_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return SHL_OK;
+}
+
+int shl_destroy(shl_ctx *ctx) {
+    if (!ctx) return SHL_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ws_free_all(ctx);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SHL_OK;
+}
+
+const char *shl_last_error(shl_ctx *ctx) { return ctx ? ctx->err.c_str() : global_err().msg.c_str(); }
+
+int shl_field(shl_ctx *ctx, const shl_design *d, int32_t r, double *F_dev, double *gradF_dev, void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!d) return set_err(ctx, SHL_EINVAL, "design is NULL");
+    shl_design dd = *d;
+    if (!(dd.t > 0.0)) dd.t = 1.0;  // no shell needed for the field alone
+    SHL_TRY(validate_design(ctx, &dd, r));
+    if (!F_dev) return set_err(ctx, SHL_EINVAL, "F_dev is NULL");
+    cudaSetDevice(ctx->device);
+    return run_field(ctx, d, r, F_dev, gradF_dev, nullptr, pick_stream(ctx, stream));
+}
+
+int shl_voxelize(shl_ctx *ctx, const shl_design *d, int32_t r, double kappa, uint8_t *mask_dev, double *rho_dev,
+                 double *d_dev, double *t_out, double *margin_out, int64_t *n_solid, int64_t *n_ambiguous,
+                 void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    SHL_TRY(validate_design(ctx, d, r));
+    cudaSetDevice(ctx->device);
+    VoxOut v;
+    SHL_TRY(run_voxelize(ctx, d, r, kappa, mask_dev, rho_dev, d_dev, pick_stream(ctx, stream), &v));
+    if (t_out) *t_out = v.t;
+    if (margin_out) *margin_out = v.margin;
+    if (n_solid) *n_solid = v.n_solid;
+    if (n_ambiguous) *n_ambiguous = v.n_amb;
+    return SHL_OK;
+}
+
+int shl_apply(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+              double E_void, int32_t precision, int32_t nvec, const void *p_dev, void *q_dev, void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (r < 1 || r > 1024) return set_err(ctx, SHL_EINVAL, "grid size r=%d out of range [1, 1024]", r);
+    if (nvec < 1 || nvec > 6) return set_err(ctx, SHL_EINVAL, "nvec=%d out of range [1, 6]", nvec);
+    if (!p_dev || !q_dev || (!mask_dev && !rho_dev)) return set_err(ctx, SHL_EINVAL, "NULL buffer");
+    if (!(nu > -1.0 && nu < 0.5)) return set_err(ctx, SHL_EINVAL, "Poisson ratio %g outside (-1, 0.5)", nu);
+    cudaSetDevice(ctx->device);
+    Density den{mask_dev, rho_dev, E, E_void};
+    cudaStream_t s = pick_stream(ctx, stream);
+    if (precision == SHL_FP64) {
+        ElemOp<double> op;
+        SHL_TRY(get_op(ctx, nu, r, &op));
+        ApplyArgs<double> a = make_apply<double>(r, den, op);
+        a.nvec = nvec;
+        a.p = static_cast<const double *>(p_dev);
+        a.q = static_cast<double *>(q_dev);
+        return launch_apply<double>(ctx, a, s);
+    } else if (precision == SHL_FP32_REFINE) {
+        ElemOp<float> op;
+        SHL_TRY(get_op(ctx, nu, r, &op));
+        ApplyArgs<float> a = make_apply<float>(r, den, op);
+        a.nvec = nvec;
+        a.p = static_cast<const float *>(p_dev);
+        a.q = static_cast<float *>(q_dev);
+        return launch_apply<float>(ctx, a, s);
+    }
+    return set_err(ctx, SHL_EINVAL, "unknown precision %d", precision);
+}
+
+int shl_rhs(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+            double E_void, double *f_dev, void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (r < 1 || r > 1024) return set_err(ctx, SHL_EINVAL, "grid size r=%d out of range [1, 1024]", r);
+    if (!f_dev || (!mask_dev && !rho_dev)) return set_err(ctx, SHL_EINVAL, "NULL buffer");
+    cudaSetDevice(ctx->device);
+    ElemOp<double> op;
+    SHL_TRY(get_op(ctx, nu, r, &op));
+    const size_t N = (size_t)r * r * r;
+    rhs_kernel<<<grid1d(N), kBlk, 0, pick_stream(ctx, stream)>>>(r, mask_dev, rho_dev, E, E_void, op, f_dev);
+    SHL_CUDA(ctx, cudaGetLastError());
+    return SHL_OK;
+}
+
+int shl_chom(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+             double E_void, const double *u_dev, double *C_out, void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (r < 1 || r > 1024) return set_err(ctx, SHL_EINVAL, "grid size r=%d out of range [1, 1024]", r);
+    if (!u_dev || !C_out || (!mask_dev && !rho_dev)) return set_err(ctx, SHL_EINVAL, "NULL buffer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = pick_stream(ctx, stream);
+    double *Cd = nullptr;
+    SHL_TRY(ws_get_t(ctx, "chom_out", 36, &Cd));
+    Density den{mask_dev, rho_dev, E, E_void};
+    SHL_TRY(run_chom(ctx, r, den, nu, u_dev, Cd, s));
+    SHL_CUDA(ctx, cudaMemcpyAsync(C_out, Cd, 36 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    return SHL_OK;
+}
+
+int shl_solve(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_dev, const shl_solve_opts *o,
+              double *u_dev, double *C_out, shl_stats *st, void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    SHL_TRY(validate_solve_opts(ctx, o));
+    if (r < 2 || r > 1024) return set_err(ctx, SHL_EINVAL, "grid size r=%d out of range [2, 1024]", r);
+    if (!mask_dev && !rho_dev) return set_err(ctx, SHL_EINVAL, "no density given");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = pick_stream(ctx, stream);
+    const size_t NV = (size_t)18 * r * r * r;
+    double *x64 = u_dev;
+    if (!x64) SHL_TRY(ws_get_t(ctx, "x64", NV, &x64));
+    Density den{mask_dev, rho_dev, o->E, o->E_void};
+    SolveOut so;
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventRecord(e0, s);
+    int rc = run_solve(ctx, r, den, o, x64, o->warm_start && u_dev, s, &so);
+    cudaEventRecord(e1, s);
+    double *Cd = nullptr;
+    if (rc == SHL_OK) rc = ws_get_t(ctx, "chom_out", 36, &Cd);
+    if (rc == SHL_OK) rc = run_chom(ctx, r, den, o->nu, x64, Cd, s);
+    cudaEventRecord(e2, s);
+    if (rc == SHL_OK && C_out) cudaMemcpyAsync(C_out, Cd, 36 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        for (int k = 0; k < 6; ++k) {
+            st->iters[k] = so.iters[k];
+            st->relres[k] = so.relres[k];
+        }
+        st->n_refine = so.n_refine;
+        st->status = rc != SHL_OK ? rc : so.status;
+        cudaEventElapsedTime(&st->ms_solve, e0, e1);
+        cudaEventElapsedTime(&st->ms_chom, e1, e2);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (rc != SHL_OK) return rc;
+    if (so.status == SHL_ENUMERIC) return set_err(ctx, SHL_ENUMERIC, "NaN/Inf in the solve");
+    if (so.status == SHL_ENOCONV) return set_err(ctx, SHL_ENOCONV, "a load case did not reach tol");
+    return SHL_OK;
+}
+
+int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, double *C_out,
+                   shl_stats *st) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    SHL_TRY(validate_solve_opts(ctx, o));
+    SHL_TRY(validate_design(ctx, d, r));
+    if (!C_out) return set_err(ctx, SHL_EINVAL, "C_out is NULL");
+    cudaSetDevice(ctx->device);
+    uint8_t *mask = nullptr;
+    double *rho = nullptr;
+    const size_t N = (size_t)r * r * r;
+    SHL_TRY(ws_get_t(ctx, "hom_mask", N, &mask));
+    if (o->density == SHL_SMOOTH) SHL_TRY(ws_get_t(ctx, "hom_rho", N, &rho));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, ctx->stream);
+    VoxOut v;
+    int rc = run_voxelize(ctx, d, r, o->kappa, mask, rho, nullptr, ctx->stream, &v);
+    cudaEventRecord(e1, ctx->stream);
+    if (rc == SHL_OK)
+        rc = shl_solve(ctx, r, o->density == SHL_SMOOTH ? nullptr : mask, rho, o, nullptr, C_out, st, nullptr);
+    if (st) {
+        cudaEventElapsedTime(&st->ms_field, e0, e1);
+        st->t = v.t;
+        st->margin = v.margin;
+        st->n_solid = v.n_solid;
+        st->n_ambiguous = v.n_amb;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
+                         double *C_out, shl_stats *st) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    if (n < 0 || (n > 0 && (!d || !r || !C_out))) return set_err(ctx, SHL_EINVAL, "bad batch arguments");
+    int worst = SHL_OK;
+    for (int i = 0; i < n; ++i) {
+        int rc = shl_homogenize(ctx, d + i, r[i], o, C_out + 36 * i, st ? st + i : nullptr);
+        if (rc != SHL_OK && rc != SHL_ENOCONV) return rc;
+        if (rc != SHL_OK) worst = rc;
+    }
+    return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libshl (include/shl.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Device buffers are torch CUDA tensors (their data_ptr() is passed); host
+outputs are numpy arrays.  The library must have been built
+(``paper_2511_04025_b300.build``); loading fails loudly otherwise, and there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libshl.so")
+
+SHL_OK, SHL_EINVAL, SHL_ENOMEM, SHL_ENOCONV, SHL_ENUMERIC, SHL_ECUDA, SHL_EAGAIN, SHL_ENOTFOUND = range(8)
+SHL_FP64, SHL_FP32_REFINE = 0, 1
+SHL_MASK, SHL_SMOOTH = 0, 1
+STATUS_NAMES = ["SHL_OK", "SHL_EINVAL", "SHL_ENOMEM", "SHL_ENOCONV", "SHL_ENUMERIC", "SHL_ECUDA", "SHL_EAGAIN",
+                "SHL_ENOTFOUND"]
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class shl_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class shl_design(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("K", ctypes.c_int32), ("pos", _dp), ("q", _dp), ("alpha", _dp),
+                ("iso", ctypes.c_double), ("t", ctypes.c_double), ("vf", ctypes.c_double)]
+
+
+class shl_solve_opts(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("E_void", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("density", ctypes.c_int32), ("warm_start", ctypes.c_int32), ("kappa", ctypes.c_double),
+                ("inner_tol", ctypes.c_double)]
+
+
+class shl_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32 * 6), ("relres", ctypes.c_double * 6), ("n_refine", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("t", ctypes.c_double), ("margin", ctypes.c_double),
+                ("n_solid", ctypes.c_int64), ("n_ambiguous", ctypes.c_int64), ("ms_field", ctypes.c_float),
+                ("ms_rhs", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_chom", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return dict(iters=list(self.iters), relres=list(self.relres), n_refine=self.n_refine, status=self.status,
+                    t=self.t, margin=self.margin, n_solid=self.n_solid, n_ambiguous=self.n_ambiguous,
+                    ms_field=self.ms_field, ms_solve=self.ms_solve, ms_chom=self.ms_chom)
+
+
+# Every symbol include/shl.h declares, with its ctypes signature.
+SIGNATURES = {
+    "shl_create": (ctypes.c_int, [ctypes.POINTER(shl_opts), ctypes.POINTER(_vp)]),
+    "shl_destroy": (ctypes.c_int, [_vp]),
+    "shl_last_error": (ctypes.c_char_p, [_vp]),
+    "shl_default_solve_opts": (None, [ctypes.POINTER(shl_solve_opts)]),
+    "shl_field": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32, _vp, _vp, _vp]),
+    "shl_voxelize": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp,
+                                    _dp, _dp, _i64p, _i64p, _vp]),
+    "shl_apply": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]),
+    "shl_rhs": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               _vp, _vp]),
+    "shl_chom": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                _vp, _dp, _vp]),
+    "shl_solve": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.POINTER(shl_solve_opts), _vp, _dp,
+                                 ctypes.POINTER(shl_stats), _vp]),
+    "shl_homogenize": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32,
+                                      ctypes.POINTER(shl_solve_opts), _dp, ctypes.POINTER(shl_stats)]),
+    "shl_homogenize_batch": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(shl_design),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(shl_solve_opts), _dp,
+                                            ctypes.POINTER(shl_stats)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libshl.so (no GPU needed to load).  Raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libshl.so not built at {LIB_PATH}: run paper_2511_04025_b300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class ShlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _check(ctx, st: int, ok=(SHL_OK,)):
+    if st not in ok:
+        raise ShlError(st, lib().shl_last_error(ctx).decode())
+    return st
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class DesignArg:
+    """Keeps the numpy arrays of a design alive while the C struct points at them."""
+
+    def __init__(self, d, t: Optional[float] = None):
+        self.pos = np.ascontiguousarray(d.pos, dtype=np.float64)
+        self.q = np.ascontiguousarray(d.q, dtype=np.float64)
+        self.alpha = None if d.alpha is None else np.ascontiguousarray(d.alpha, dtype=np.float64)
+        tt = t if t is not None else (d.t if d.t is not None else 0.0)
+        self.s = shl_design(
+            n=self.pos.shape[0], K=d.K, pos=self.pos.ctypes.data_as(_dp), q=self.q.ctypes.data_as(_dp),
+            alpha=self.alpha.ctypes.data_as(_dp) if self.alpha is not None else None, iso=float(d.iso),
+            t=float(tt), vf=float(d.vf if d.vf is not None else 0.0))
+
+
+def default_solve_opts(**kw) -> shl_solve_opts:
+    o = shl_solve_opts()
+    lib().shl_default_solve_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C entry points
+# ---------------------------------------------------------------------------
+
+def shl_create(device: int = 0, max_batch: int = 0, hbm_budget_bytes: int = 0) -> int:
+    o = shl_opts(device=device, max_batch=max_batch, hbm_budget_bytes=hbm_budget_bytes)
+    out = _vp()
+    st = lib().shl_create(ctypes.byref(o), ctypes.byref(out))
+    if st != SHL_OK:
+        raise ShlError(st, lib().shl_last_error(None).decode())
+    return out.value
+
+
+def shl_destroy(ctx: int) -> None:
+    lib().shl_destroy(ctx)
+
+
+def shl_field(ctx, design, r: int, F, gradF=None, stream=None):
+    d = DesignArg(design)
+    _check(ctx, lib().shl_field(ctx, ctypes.byref(d.s), r, _ptr(F), _ptr(gradF), _stream(stream)))
+
+
+def shl_voxelize(ctx, design, r: int, kappa: float = 0.0, mask=None, rho=None, d=None, t: Optional[float] = None,
+                 stream=None) -> dict:
+    da = DesignArg(design, t)
+    tt, mg = ctypes.c_double(), ctypes.c_double()
+    ns, na = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib().shl_voxelize(ctx, ctypes.byref(da.s), r, kappa, _ptr(mask), _ptr(rho), _ptr(d),
+                                   ctypes.byref(tt), ctypes.byref(mg), ctypes.byref(ns), ctypes.byref(na),
+                                   _stream(stream)))
+    return dict(t=tt.value, margin=mg.value, n_solid=ns.value, n_ambiguous=na.value)
+
+
+def shl_apply(ctx, r: int, p, q, mask=None, rho=None, E=1.0, nu=0.3, E_void=1e-6, precision=None, nvec=None,
+              stream=None):
+    import torch
+    if precision is None:
+        precision = SHL_FP64 if p.dtype == torch.float64 else SHL_FP32_REFINE
+    if nvec is None:
+        nvec = p.shape[0] // 3
+    _check(ctx, lib().shl_apply(ctx, r, _ptr(mask), _ptr(rho), E, nu, E_void, precision, nvec, _ptr(p), _ptr(q),
+                                _stream(stream)))
+
+
+def shl_rhs(ctx, r: int, f, mask=None, rho=None, E=1.0, nu=0.3, E_void=1e-6, stream=None):
+    _check(ctx, lib().shl_rhs(ctx, r, _ptr(mask), _ptr(rho), E, nu, E_void, _ptr(f), _stream(stream)))
+
+
+def shl_chom(ctx, r: int, u, mask=None, rho=None, E=1.0, nu=0.3, E_void=1e-6, stream=None) -> np.ndarray:
+    C = np.zeros(36)
+    _check(ctx, lib().shl_chom(ctx, r, _ptr(mask), _ptr(rho), E, nu, E_void, _ptr(u), C.ctypes.data_as(_dp),
+                               _stream(stream)))
+    return C.reshape(6, 6)
+
+
+def shl_solve(ctx, r: int, opts: shl_solve_opts, mask=None, rho=None, u=None, stream=None):
+    C = np.zeros(36)
+    st = shl_stats()
+    rc = lib().shl_solve(ctx, r, _ptr(mask), _ptr(rho), ctypes.byref(opts), _ptr(u), C.ctypes.data_as(_dp),
+                         ctypes.byref(st), _stream(stream))
+    _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
+    return C.reshape(6, 6), st.as_dict()
+
+
+def shl_homogenize(ctx, design, r: int, opts: shl_solve_opts, t: Optional[float] = None):
+    d = DesignArg(design, t)
+    C = np.zeros(36)
+    st = shl_stats()
+    rc = lib().shl_homogenize(ctx, ctypes.byref(d.s), r, ctypes.byref(opts), C.ctypes.data_as(_dp),
+                              ctypes.byref(st))
+    _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
+    return C.reshape(6, 6), st.as_dict()
+
+
+def shl_homogenize_batch(ctx, designs: Sequence, rs: Sequence[int], opts: shl_solve_opts):
+    args = [DesignArg(d) for d in designs]
+    arr = (shl_design * len(args))(*[a.s for a in args])
+    r_arr = (ctypes.c_int32 * len(args))(*rs)
+    C = np.zeros(36 * len(args))
+    st = (shl_stats * len(args))()
+    rc = lib().shl_homogenize_batch(ctx, len(args), arr, r_arr, ctypes.byref(opts), C.ctypes.data_as(_dp), st)
+    _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
+    return C.reshape(-1, 6, 6), [s.as_dict() for s in st]
+
+
+class Context:
+    """Owns one shl_ctx (closed on exit or garbage collection)."""
+
+    def __init__(self, device: int = 0, **kw):
+        self.handle = shl_create(device, **kw)
+
+    def close(self):
+        if self.handle:
+            shl_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,224 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances (derived in the design doc):
+  * field F, grad F: FP64 on both sides, different summation orders ->
+    |dF| <= 1e-12 max|F|;
+  * mask: bit-exact (t sits mid-gap; the ambiguous count must be 0);
+  * stiffness apply / loads: FP64 1e-12, FP32 2e-6 relative to max|K p|;
+  * C^H: entry error |dC_ij| / max(|C_ij|, 1e-2 max|C|) <= 1e-9 in the FP64
+    mode and <= 1e-4 in FP32 + refinement, against the oracle solved to 1e-12.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2511_04025_b300 import inputs  # noqa: E402
+from paper_2511_04025_b300 import shl  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device: GPU tests need a B300")
+    c = shl.Context(0)
+    yield c.handle
+    c.close()
+
+
+def entry_err(C, Cref):
+    s = np.abs(Cref).max()
+    return np.max(np.abs(C - Cref) / np.maximum(np.abs(Cref), 1e-2 * s))
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name + ".json")) as f:
+        g = json.load(f)
+    g["C"] = np.array(g["C"])
+    return g
+
+
+# --------------------------------------------------------------------------- #
+# field + voxelisation
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("r,mk,alpha", [(32, inputs.plain_32, False), (20, inputs.gaussian_64, True),
+                                        (37, inputs.plain_32, False)])
+def test_field_matches_oracle(ctx, r, mk, alpha):
+    d = mk(3)
+    if alpha:
+        d.alpha = np.random.default_rng(5).uniform(0.3, 1.7, size=64)
+        d.iso = 0.01
+    F = torch.empty(r ** 3, dtype=torch.float64, device=DEV)
+    gF = torch.empty(r ** 3, 3, dtype=torch.float64, device=DEV)
+    shl.shl_field(ctx, d, r, F, gF)
+    torch.cuda.synchronize()
+    Fo, gFo = oracle.field_grid(d, r)
+    assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-12 * np.abs(Fo).max()
+    assert np.abs(gF.cpu().numpy() - gFo).max() <= 1e-12 * np.abs(gFo).max()
+
+
+@pytest.mark.parametrize("r,mk,seed", [(32, inputs.plain_32, 0), (64, inputs.gaussian_64, 0),
+                                       (48, inputs.cubic_128, 0), (33, inputs.plain_32, 2)])
+def test_voxelize_mask_bit_exact(ctx, r, mk, seed):
+    d = mk(seed)
+    mask = torch.empty(r ** 3, dtype=torch.uint8, device=DEV)
+    dd = torch.empty(r ** 3, dtype=torch.float64, device=DEV)
+    out = shl.shl_voxelize(ctx, d, r, mask=mask, d=dd)
+    vox = oracle.voxelize(d, r)
+    assert out["n_ambiguous"] == 0 and vox["ambiguous"] == 0
+    assert abs(out["t"] - vox["t"]) <= 1e-12 * vox["t"]
+    assert out["n_solid"] == int(vox["mask"].sum())
+    assert np.array_equal(mask.cpu().numpy(), vox["mask"])
+    np.testing.assert_allclose(dd.cpu().numpy(), vox["d"], rtol=1e-9, atol=1e-14)
+
+
+def test_voxelize_explicit_t_and_smooth_density(ctx):
+    r = 24
+    d = inputs.plain_32(1)
+    vox = oracle.voxelize(d, r)
+    t = vox["t"]
+    mask = torch.empty(r ** 3, dtype=torch.uint8, device=DEV)
+    rho = torch.empty(r ** 3, dtype=torch.float64, device=DEV)
+    kap = oracle.default_kappa(r)
+    out = shl.shl_voxelize(ctx, d, r, kappa=kap, mask=mask, rho=rho, t=t)
+    assert out["t"] == t
+    assert np.array_equal(mask.cpu().numpy(), vox["mask"])
+    np.testing.assert_allclose(rho.cpu().numpy(), oracle.beta(vox["d"], t, kap), rtol=1e-11, atol=1e-14)
+
+
+def test_voxelize_cubic_128_full_size(ctx):
+    """The 128^3 O_h workload at full size: mask bit-exact and O_h invariant."""
+    r = 128
+    d = inputs.cubic_128(0)
+    mask = torch.empty(r ** 3, dtype=torch.uint8, device=DEV)
+    out = shl.shl_voxelize(ctx, d, r, mask=mask)
+    vox = oracle.voxelize(d, r)
+    m = mask.cpu().numpy()
+    assert out["n_ambiguous"] == 0 and out["n_solid"] == int(vox["mask"].sum())
+    assert np.array_equal(m, vox["mask"])
+    m3 = m.reshape(r, r, r)
+    assert np.array_equal(m3, m3.transpose(1, 0, 2)) and np.array_equal(m3, m3[:, :, ::-1])
+
+
+# --------------------------------------------------------------------------- #
+# stiffness apply, loads
+# --------------------------------------------------------------------------- #
+
+def _rand_mask(r, seed, frac=0.3):
+    return (np.random.default_rng(seed).uniform(size=r ** 3) < frac).astype(np.uint8)
+
+
+@pytest.mark.parametrize("r", [2, 3, 5, 16, 20, 33])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_apply_matches_assembled_oracle(ctx, r, dtype):
+    m = _rand_mask(r, r)
+    rng = np.random.default_rng(100 + r)
+    x = rng.standard_normal((6, r ** 3, 3))
+    y = oracle.apply(r, m.astype(np.float64), x)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    p = torch.tensor(oracle.aos_to_soa(x), dtype=td, device=DEV)
+    q = torch.zeros_like(p)
+    shl.shl_apply(ctx, r, p, q, mask=torch.tensor(m, device=DEV))
+    torch.cuda.synchronize()
+    yq = oracle.soa_to_aos(q.double().cpu().numpy())
+    tol = 1e-12 if dtype == "f64" else 2e-6
+    assert np.abs(yq - y).max() <= tol * np.abs(y).max()
+
+
+def test_apply_smooth_density_and_subset_of_load_cases(ctx):
+    r = 18
+    rho = np.random.default_rng(7).uniform(size=r ** 3)
+    x = np.random.default_rng(8).standard_normal((2, r ** 3, 3))
+    y = oracle.apply(r, rho, x, E=2.0, nu=0.25, Evoid=1e-3)
+    p = torch.tensor(oracle.aos_to_soa(x), device=DEV)
+    q = torch.zeros_like(p)
+    shl.shl_apply(ctx, r, p, q, rho=torch.tensor(rho, device=DEV), E=2.0, nu=0.25, E_void=1e-3, nvec=2)
+    torch.cuda.synchronize()
+    assert np.abs(oracle.soa_to_aos(q.cpu().numpy()) - y).max() <= 1e-12 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("r", [4, 32])
+def test_rhs_matches_oracle(ctx, r):
+    m = _rand_mask(r, 3)
+    f = oracle.rhs(r, m.astype(np.float64))
+    fd = torch.zeros(18, r ** 3, dtype=torch.float64, device=DEV)
+    shl.shl_rhs(ctx, r, fd, mask=torch.tensor(m, device=DEV))
+    torch.cuda.synchronize()
+    assert np.abs(oracle.soa_to_aos(fd.cpu().numpy()) - f).max() <= 1e-13 * np.abs(f).max()
+
+
+def test_chom_from_given_displacements(ctx):
+    r = 12
+    m = _rand_mask(r, 11, 0.4)
+    u = np.random.default_rng(12).standard_normal((6, r ** 3, 3)) * 0.01
+    C, _ = oracle.chom(r, m.astype(np.float64), u)
+    Cg = shl.shl_chom(ctx, r, torch.tensor(oracle.aos_to_soa(u), device=DEV), mask=torch.tensor(m, device=DEV))
+    assert np.abs(Cg - C).max() <= 1e-13 * np.abs(C).max()
+
+
+# --------------------------------------------------------------------------- #
+# whole path
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("name,seed", [("plain32_s0", 0), ("plain32_s1", 1)])
+def test_homogenize_fp64_matches_oracle(ctx, name, seed):
+    g = gold(name)
+    d = inputs.plain_32(seed)
+    C, st = shl.shl_homogenize(ctx, d, 32, shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP64))
+    assert st["status"] == 0 and st["n_ambiguous"] == 0
+    assert st["n_solid"] == g["n_solid"]
+    assert max(st["relres"]) <= 1e-10
+    assert np.abs(C - C.T).max() <= 1e-14 * np.abs(C).max()
+    assert entry_err(C, g["C"]) <= 1e-9
+
+
+@pytest.mark.parametrize("name,seed", [("plain32_s0", 0), ("plain32_s1", 1)])
+def test_homogenize_fp32_refine_matches_oracle(ctx, name, seed):
+    g = gold(name)
+    d = inputs.plain_32(seed)
+    C, st = shl.shl_homogenize(ctx, d, 32, shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP32_REFINE))
+    assert st["status"] == 0 and st["n_refine"] >= 1
+    assert max(st["relres"]) <= 1e-10
+    assert entry_err(C, g["C"]) <= 1e-4
+    assert entry_err(C, g["C"]) <= 1e-9  # refinement restores the FP64 level
+
+
+def test_solid_cell_returns_base_tensor(ctx):
+    r = 16
+    m = torch.ones(r ** 3, dtype=torch.uint8, device=DEV)
+    C, st = shl.shl_solve(ctx, r, shl.default_solve_opts(), mask=m)
+    np.testing.assert_allclose(C, oracle.isotropic_C(), rtol=1e-12, atol=1e-15)
+
+
+def test_laminate_fp32_refine(ctx):
+    r = 16
+    layers = (np.arange(r) % 4 < 1).astype(np.uint8)
+    m = np.repeat(layers, r * r)
+    u, *_ = oracle.solve(r, m.astype(np.float64), tol=1e-12)
+    Cref, _ = oracle.chom(r, m.astype(np.float64), u)
+    C, st = shl.shl_solve(ctx, r, shl.default_solve_opts(precision=shl.SHL_FP32_REFINE),
+                          mask=torch.tensor(m, device=DEV))
+    assert entry_err(C, Cref) <= 1e-8
+
+
+def test_invalid_arguments_rejected(ctx):
+    d = inputs.plain_32(0)
+    bad = d.copy(vf=None)
+    with pytest.raises(shl.ShlError) as e:
+        shl.shl_homogenize(ctx, bad, 32, shl.default_solve_opts())
+    assert e.value.status == shl.SHL_EINVAL
+    with pytest.raises(shl.ShlError) as e:
+        shl.shl_homogenize(ctx, d, 1, shl.default_solve_opts())
+    assert e.value.status == shl.SHL_EINVAL
+    with pytest.raises(shl.ShlError) as e:
+        shl.shl_homogenize(ctx, d, 16, shl.default_solve_opts(nu=0.5))
+    assert e.value.status == shl.SHL_EINVAL
