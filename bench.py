@@ -1,0 +1,307 @@
+"""Benchmark: homogenised designs/sec (6x6 C^H) on synthetic shell designs.
+
+One step = the whole path for one design: field -> distance -> threshold ->
+mask -> six periodic cell problems (FP32 PCG + FP64 residual refinement to a
+1e-10 relative residual) -> C^H, through the C-ABI call shl_homogenize.
+
+Default workload: 64^3 grid, 32 charges uniform in the cell with magnitudes
+N(0,1), 8 % solid volume (seeded synthetic designs; the paper's datasets are
+not available).  Multi-GPU: independent replicas (designs are independent),
+one process per GPU, weak scaling, no data-path collective.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl shl|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, r, description)
+    "gaussian64": ("gaussian_64", 64, "64^3 grid, 32 charges uniform, q~N(0,1), 8% solid"),
+    "cubic128": ("cubic_128", 128, "128^3 grid, 48 charges (O_h orbit), 5% solid"),
+    "plain32": ("plain_32", 32, "32^3 grid, 8 charges +-1, 15% solid"),
+}
+APPLY_BYTES_PER_NODE_F32 = 72 + 72 + 1  # read p (18 floats), write q (18 floats), 1 mask byte
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes per launch of the FP32 stiffness apply at 64^3 from one ncu
+# capture (profiles/apply_fp32_64.md); None until measured for the current kernel.
+APPLY_TRAFFIC_64 = None
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(design, r, golden_iters):
+    """The FP64 oracle as it stands on a bounded sample of one design: full
+    field/voxelisation, assembly, a fixed number of PCG iterations and C^H,
+    scaled to a whole design by the oracle's own iteration count."""
+    import oracle
+    t0 = time.perf_counter()
+    vox = oracle.voxelize(design, r)
+    t_vox = time.perf_counter() - t0
+    rho = vox["mask"].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.solve(r, rho, tol=1e-300, maxit=0)
+    t_setup = time.perf_counter() - t0
+    n_s = 60
+    t0 = time.perf_counter()
+    u, *_ = oracle.solve(r, rho, tol=1e-300, maxit=n_s)
+    t_it = (time.perf_counter() - t0 - t_setup) / n_s
+    t0 = time.perf_counter()
+    oracle.chom(r, rho, u)
+    t_c = time.perf_counter() - t0
+    per_design = t_vox + t_setup + golden_iters * t_it + t_c
+    sample = (f"oracle on one {r}^3 design: field+voxelise, assembly, {n_s} PCG iterations and C^H timed; "
+              f"iterations scaled to {golden_iters} (the oracle's own count to 1e-12 on the seed-0 design)")
+    return 1.0 / per_design, per_design, sample, oracle.num_threads()
+
+
+def golden_iters(workload):
+    fn = os.path.join(ROOT, "tests", "golden", {"gaussian64": "gaussian64_s0", "plain32": "plain32_s0"}
+                      .get(workload, "gaussian64_s0") + ".json")
+    try:
+        with open(fn) as f:
+            return int(max(json.load(f)["iters"]))
+    except Exception:
+        return 5000
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    return rank, world, local
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, each step a bounded sample."""
+    rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    from paper_2511_04025_b300 import inputs
+    gen, r, desc = WORKLOADS[args.workload]
+    gi = golden_iters(args.workload)
+    for i in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not needed
+    times = []
+    sample = cores = None
+    for i in range(args.steps):
+        d = getattr(inputs, gen)(i)
+        v, per, sample, cores = oracle_sample(d, r, gi)
+        times.append(per)
+    value = args.steps / sum(times)
+    line = {"metric": "homogenized designs/sec", "value": value, "unit": "designs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": desc, "r": r, "tol": 1e-12},
+            "cpu_baseline": {"value": value, "unit": "designs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "designs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="shl", choices=["shl", "reference"])
+    ap.add_argument("--workload", default="gaussian64", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    gen, r, desc = WORKLOADS[args.workload]
+    prec = shl.SHL_FP32_REFINE if args.precision == "fp32r" else shl.SHL_FP64
+    opts = shl.default_solve_opts(precision=prec, tol=1e-10)
+    ctx = shl.Context(local)
+    h = ctx.handle
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
+    designs = [getattr(inputs, gen)(100000 * rank + i) for i in range(args.warmup + args.steps)]
+
+    for i in range(args.warmup):
+        shl.shl_homogenize(h, designs[i], r, opts, stream=stream)
+    torch.cuda.synchronize()
+    c0 = shl.shl_get_counters(h)["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall = []
+    stats = []
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.add_(1.0)  # L2 flush between timed steps (untimed)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            ev[k][0].record(stream)
+            C, st = shl.shl_homogenize(h, designs[args.warmup + k], r, opts, stream=stream)
+            ev[k][1].record(stream)
+            stream.synchronize()
+            wall.append(time.perf_counter() - t0)
+            stats.append(st)
+    torch.cuda.synchronize()
+    c1 = shl.shl_get_counters(h)["kernel_launches"]
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    wall_s = sum(wall)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_s, wall_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s, wall_s = float(t[0]), float(t[1])
+    value = world * args.steps / dev_s
+    e2e = world * args.steps / wall_s
+
+    # dominant kernel: the FP32 stiffness apply of the inner solves, timed live
+    # on the launch stream on the last design's mask
+    N = r ** 3
+    mask = torch.empty(N, dtype=torch.uint8, device="cuda")
+    shl.shl_voxelize(h, designs[-1], r, mask=mask, stream=stream)
+    p = torch.randn(18, N, dtype=torch.float32, device="cuda")
+    q = torch.empty_like(p)
+    for _ in range(5):
+        shl.shl_apply(h, r, p, q, mask=mask, stream=stream)
+    L = 50
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(L):
+        shl.shl_apply(h, r, p, q, mask=mask, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    apply_s = a0.elapsed_time(a1) / 1e3 / L
+    peak, peak_kind = peaks()
+    achieved = APPLY_BYTES_PER_NODE_F32 * N / apply_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": "apply_kernel<float> (stiffness apply)",
+                "peak_kind": peak_kind, "launch_us": apply_s * 1e6}
+
+    compare = None
+    if not args.no_compare and prec == shl.SHL_FP32_REFINE and rank == 0:
+        o64 = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C64, st64 = shl.shl_homogenize(h, designs[-1], r, o64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s64 = e0.elapsed_time(e1) / 1e3
+        Cm = C
+        err = float(np.max(np.abs(Cm - C64) / np.maximum(np.abs(C64), 1e-2 * np.abs(C64).max())))
+        compare = {"fp64_designs_per_s": 1.0 / s64, "fp64_iters": max(st64["iters"]),
+                   "fp32r_vs_fp64_entry_err": err}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, per, sample, cores = oracle_sample(designs[0], r, golden_iters(args.workload))
+        cpu = {"value": v, "unit": "designs/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        d0 = designs[args.warmup]
+        line = {
+            "metric": "homogenized designs/sec", "value": value, "unit": "designs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "r": r, "precision": args.precision,
+                       "tol": 1e-10, "l2": "flushed between steps", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e, "unit": "designs/s", "h2d_bytes_per_step": int(d0.pos.nbytes + d0.q.nbytes),
+                    "d2h_bytes_per_step": 36 * 8},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": int(c1 - c0),
+            "solver": {"iters_max": [max(s["iters"]) for s in stats], "n_refine": [s["n_refine"] for s in stats],
+                       "relres_max": max(max(s["relres"]) for s in stats)},
+            "compare": compare,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -213,11 +213,19 @@ int shl_solve(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rh
  * still written).
  */
 int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, double *C_out,
-                   shl_stats *st);
+                   shl_stats *st, void *stream);
 
 /* n designs, each on its own r[i]^3 grid; C_out: n x 36; st: n records or NULL. */
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
-                         double *C_out, shl_stats *st);
+                         double *C_out, shl_stats *st, void *stream);
+
+/* Telemetry of a context since creation: kernels launched by the library and
+ * device workspace bytes currently held.  No device work. */
+typedef struct {
+    uint64_t kernel_launches;
+    uint64_t workspace_bytes;
+} shl_counters;
+int shl_get_counters(shl_ctx *ctx, shl_counters *out);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,7 @@ struct shl_ctx {
     shl_workspace ws;
     std::recursive_mutex mu;  // serialises public calls on one context
     void *serve = nullptr;    // serving scheduler state (serve.cuh)
+    unsigned long long launches = 0;  // kernels launched (telemetry)
 };
 
 namespace shl {

@@ -59,6 +59,7 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
         }
     }
     apply_kernel<T, kTX, kTY><<<g, Shape::THREADS, Shape::smem<T>(), s>>>(a);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
 }
@@ -113,6 +114,7 @@ inline int run_field(shl_ctx *ctx, const shl_design *d, int r, double *F, double
     double *A = nullptr;
     SHL_TRY(ws_get_t(ctx, "field_A", (size_t)nb * nb * nb, &A));
     field_coef_kernel<<<1, 512, 0, s>>>(d->n, d->K, u.pos, u.q, u.alpha, A);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     int lines = r;
     while (lines > 1 && field_smem_bytes(r, d->K, lines) > 96 * 1024) lines = (lines + 1) / 2;
@@ -121,6 +123,7 @@ inline int run_field(shl_ctx *ctx, const shl_design *d, int r, double *F, double
     const size_t smem = field_smem_bytes(r, d->K, lines);
     cudaFuncSetAttribute(field_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     field_grid_kernel<<<dim3(r, (r + lines - 1) / lines), 256, smem, s>>>(fa);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
 }
@@ -145,9 +148,12 @@ inline int run_select(shl_ctx *ctx, const double *dd, size_t n, double vf, cudaS
     for (int p = 0; p < 6; ++p) {
         select_hist_kernel<<<g, 256, 0, s>>>(keys, n, st, shifts[p], widths[p]);
         select_choose_kernel<<<1, 256, 0, s>>>(st, shifts[p]);
+        ctx->launches += 2;
     }
     select_gather_kernel<<<g, 256, 0, s>>>(keys, n, st);
+    ++ctx->launches;
     select_finish_kernel<<<1, 1024, 0, s>>>(st, (long long)n, k0);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     // the host staging struct is reused: make sure its copy has completed
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
@@ -174,6 +180,7 @@ inline int run_voxelize(shl_ctx *ctx, const shl_design *d, int r, double kappa, 
     SHL_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
     if (kappa <= 0.0) kappa = std::log(9.0) * r;
     voxel_mask_kernel<<<grid1d(n, 256, 148 * 8), 256, 0, s>>>(dd, n, sel, d->t, kappa, mask, rho, counts);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     unsigned long long hc[2];
     SHL_CUDA(ctx, cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -256,6 +263,7 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     SHL_TRY(ws_get_t(ctx, "pcg_partial", (size_t)gv * 12, &partial));
     VecArgs<T> va{N, b.x, b.r, b.p, b.q, b.dinv, st, partial};
     pcg_init_kernel<T><<<gv, kBlk, 0, s>>>(va, want, set_bnorm);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     ApplyArgs<T> a = make_apply<T>(r, den, op);
     a.p = b.p;
@@ -272,6 +280,7 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
             SHL_TRY(launch_apply<T>(ctx, a, s));
             pcg_update_kernel<T><<<gv, kBlk, 0, s>>>(va);
             pcg_direction_kernel<T><<<gv, kBlk, 0, s>>>(va);
+            ctx->launches += 2;
         }
         SHL_CUDA(ctx, cudaGetLastError());
         SHL_CUDA(ctx, cudaMemcpyAsync(host_nactive, &st->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -347,9 +356,11 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         SHL_TRY(ws_get_t(ctx, "q64", NV, &b.q));
         SHL_TRY(ws_get_t(ctx, "dinv64", N, &b.dinv));
         dinv_kernel<double><<<grid1d(N), kBlk, 0, s>>>(r, den.mask, den.rho, den.E, den.Ev, op64.diag, b.dinv);
+        ++ctx->launches;
         PcgState *st = nullptr;
         SHL_TRY(ws_get_t(ctx, "pcg_state64", 1, &st));
         pcg_config_kernel<<<1, 32, 0, s>>>(st, tol * tol, maxit, 1);
+        ++ctx->launches;
         SHL_CUDA(ctx, cudaMemcpyAsync(st->bnorm2, norms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (warm) SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, nullptr, s));
         // CG stops on its recurrence residual, which drifts from f - K x in
@@ -385,6 +396,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         SHL_TRY(ws_get_t(ctx, "q32", NV, &b.q));
         SHL_TRY(ws_get_t(ctx, "dinv32", N, &b.dinv));
         dinv_kernel<float><<<grid1d(N), kBlk, 0, s>>>(r, den.mask, den.rho, den.E, den.Ev, op64.diag, b.dinv);
+        ++ctx->launches;
         PcgState *st = nullptr;
         SHL_TRY(ws_get_t(ctx, "pcg_state32", 1, &st));
         double *scale = nullptr;
@@ -411,9 +423,12 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             if (!want || outer >= max_outer || out->status == SHL_ENUMERIC) break;
             SHL_CUDA(ctx, cudaMemcpyAsync(scale, sc, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
             refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, scale, want, b.r, b.x);
+            ++ctx->launches;
             pcg_config_kernel<<<1, 32, 0, s>>>(st, itol * itol, maxit, 1);
+            ++ctx->launches;
             SHL_TRY(pcg_run<float>(ctx, r, den, op32, b, st, want, 1, s, hp.nactive, maxit));
             refine_gather_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, scale, want, x64);
+            ++ctx->launches;
             int its[6], nerr = 0;
             SHL_CUDA(ctx, cudaMemcpyAsync(its, st->iters, sizeof(its), cudaMemcpyDeviceToHost, s));
             SHL_CUDA(ctx, cudaMemcpyAsync(&nerr, &st->numeric_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -467,6 +482,7 @@ inline int run_chom(shl_ctx *ctx, int r, const Density &den, double nu, const do
     const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
     cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     chom_kernel<<<g, kChomThreads, smem, s>>>(a);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
 }
@@ -612,6 +628,7 @@ int shl_rhs(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho_
     SHL_TRY(get_op(ctx, nu, r, &op));
     const size_t N = (size_t)r * r * r;
     rhs_kernel<<<grid1d(N), kBlk, 0, pick_stream(ctx, stream)>>>(r, mask_dev, rho_dev, E, E_void, op, f_dev);
+    ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
 }
@@ -681,7 +698,7 @@ int shl_solve(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rh
 }
 
 int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, double *C_out,
-                   shl_stats *st) {
+                   shl_stats *st, void *stream) {
     if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     SHL_TRY(validate_solve_opts(ctx, o));
@@ -693,15 +710,16 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
     const size_t N = (size_t)r * r * r;
     SHL_TRY(ws_get_t(ctx, "hom_mask", N, &mask));
     if (o->density == SHL_SMOOTH) SHL_TRY(ws_get_t(ctx, "hom_rho", N, &rho));
+    cudaStream_t s = pick_stream(ctx, stream);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    cudaEventRecord(e0, ctx->stream);
+    cudaEventRecord(e0, s);
     VoxOut v;
-    int rc = run_voxelize(ctx, d, r, o->kappa, mask, rho, nullptr, ctx->stream, &v);
-    cudaEventRecord(e1, ctx->stream);
+    int rc = run_voxelize(ctx, d, r, o->kappa, mask, rho, nullptr, s, &v);
+    cudaEventRecord(e1, s);
     if (rc == SHL_OK)
-        rc = shl_solve(ctx, r, o->density == SHL_SMOOTH ? nullptr : mask, rho, o, nullptr, C_out, st, nullptr);
+        rc = shl_solve(ctx, r, o->density == SHL_SMOOTH ? nullptr : mask, rho, o, nullptr, C_out, st, s);
     if (st) {
         cudaEventElapsedTime(&st->ms_field, e0, e1);
         st->t = v.t;
@@ -715,16 +733,26 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
 }
 
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
-                         double *C_out, shl_stats *st) {
+                         double *C_out, shl_stats *st, void *stream) {
     if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
     if (n < 0 || (n > 0 && (!d || !r || !C_out))) return set_err(ctx, SHL_EINVAL, "bad batch arguments");
     int worst = SHL_OK;
     for (int i = 0; i < n; ++i) {
-        int rc = shl_homogenize(ctx, d + i, r[i], o, C_out + 36 * i, st ? st + i : nullptr);
+        int rc = shl_homogenize(ctx, d + i, r[i], o, C_out + 36 * i, st ? st + i : nullptr, stream);
         if (rc != SHL_OK && rc != SHL_ENOCONV) return rc;
         if (rc != SHL_OK) worst = rc;
     }
     return worst;
+}
+
+int shl_get_counters(shl_ctx *ctx, shl_counters *out) {
+    if (!ctx || !out) return set_err(ctx, SHL_EINVAL, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    out->kernel_launches = ctx->launches;
+    uint64_t b = 0;
+    for (auto &kv : ctx->ws.slots) b += kv.second.second;
+    out->workspace_bytes = b;
+    return SHL_OK;
 }
 
 }  // extern "C"

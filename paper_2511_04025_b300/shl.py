@@ -74,10 +74,11 @@ SIGNATURES = {
     "shl_solve": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.POINTER(shl_solve_opts), _vp, _dp,
                                  ctypes.POINTER(shl_stats), _vp]),
     "shl_homogenize": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32,
-                                      ctypes.POINTER(shl_solve_opts), _dp, ctypes.POINTER(shl_stats)]),
+                                      ctypes.POINTER(shl_solve_opts), _dp, ctypes.POINTER(shl_stats), _vp]),
     "shl_homogenize_batch": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(shl_design),
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(shl_solve_opts), _dp,
-                                            ctypes.POINTER(shl_stats)]),
+                                            ctypes.POINTER(shl_stats), _vp]),
+    "shl_get_counters": (ctypes.c_int, [_vp, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -211,25 +212,36 @@ def shl_solve(ctx, r: int, opts: shl_solve_opts, mask=None, rho=None, u=None, st
     return C.reshape(6, 6), st.as_dict()
 
 
-def shl_homogenize(ctx, design, r: int, opts: shl_solve_opts, t: Optional[float] = None):
+def shl_homogenize(ctx, design, r: int, opts: shl_solve_opts, t: Optional[float] = None, stream=None):
     d = DesignArg(design, t)
     C = np.zeros(36)
     st = shl_stats()
     rc = lib().shl_homogenize(ctx, ctypes.byref(d.s), r, ctypes.byref(opts), C.ctypes.data_as(_dp),
-                              ctypes.byref(st))
+                              ctypes.byref(st), _stream(stream))
     _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
     return C.reshape(6, 6), st.as_dict()
 
 
-def shl_homogenize_batch(ctx, designs: Sequence, rs: Sequence[int], opts: shl_solve_opts):
+def shl_homogenize_batch(ctx, designs: Sequence, rs: Sequence[int], opts: shl_solve_opts, stream=None):
     args = [DesignArg(d) for d in designs]
     arr = (shl_design * len(args))(*[a.s for a in args])
     r_arr = (ctypes.c_int32 * len(args))(*rs)
     C = np.zeros(36 * len(args))
     st = (shl_stats * len(args))()
-    rc = lib().shl_homogenize_batch(ctx, len(args), arr, r_arr, ctypes.byref(opts), C.ctypes.data_as(_dp), st)
+    rc = lib().shl_homogenize_batch(ctx, len(args), arr, r_arr, ctypes.byref(opts), C.ctypes.data_as(_dp), st,
+                                    _stream(stream))
     _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
     return C.reshape(-1, 6, 6), [s.as_dict() for s in st]
+
+
+class shl_counters(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+
+
+def shl_get_counters(ctx) -> dict:
+    c = shl_counters()
+    _check(ctx, lib().shl_get_counters(ctx, ctypes.byref(c)))
+    return dict(kernel_launches=c.kernel_launches, workspace_bytes=c.workspace_bytes)
 
 
 class Context:
