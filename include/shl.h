@@ -227,6 +227,29 @@ typedef struct {
 } shl_counters;
 int shl_get_counters(shl_ctx *ctx, shl_counters *out);
 
+/*
+ * Allocation-free variant of shl_chom (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate device memory, e.g. code
+ * running inside another framework's memory pool or a latency-critical loop
+ * where cudaMalloc may stall or is not permitted).  Computes the same C^H as
+ * shl_chom, but writes the 36 doubles to the device buffer C_dev (row-major)
+ * and needs no context: the reduction's scratch is a fixed 256 KiB array
+ * inside the library that every GPU loading the library holds until exit.
+ * It calls no cudaMalloc/cudaFree.
+ *   - runs on the calling thread's current device, on stream (NULL = legacy
+ *     default stream); returns without synchronising;
+ *   - 1 <= r <= 512; larger grids are rejected with SHL_EINVAL;
+ *   - the first call on each device looks up the scratch address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - all calls share the one scratch array (it keeps the last call's
+ *     contents; the call clears what must start at zero), so calls whose
+ *     work overlaps on the GPU (different streams, no ordering) race;
+ *   - errors are reported by the return code and shl_last_error(NULL).
+ * Density arguments as in shl_apply; u_dev as in shl_chom.
+ */
+int shl_chom_noalloc(int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu, double E_void,
+                     const double *u_dev, double *C_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

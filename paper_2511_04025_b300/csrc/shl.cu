@@ -756,3 +756,82 @@ int shl_get_counters(shl_ctx *ctx, shl_counters *out) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free C^H reduction (shl_chom_noalloc)
+//
+// For callers that must not allocate device memory: code that runs inside
+// another framework's memory pool or a real-time loop where cudaMalloc can
+// stall or is forbidden.  The reduction's scratch (last-block ticket and
+// per-block partial sums) lives in the file-scope array below instead of a
+// context workspace; the caller passes only inputs and the 36-double output.
+// ===========================================================================
+namespace shl {
+
+constexpr int kNoAllocMaxBlocks = 148 * 8;           // grid cap of the C^H kernel
+constexpr size_t kNoAllocScratchBytes = 256 * 1024;  // held by every GPU that loads the library
+constexpr int kNoAllocMaxR = 512;
+static_assert(256 + sizeof(double) * 21 * kNoAllocMaxBlocks <= kNoAllocScratchBytes, "scratch too small");
+
+// [0, 256): reduction ticket; [256, ...): per-block partial sums (21 doubles each).
+static __device__ __align__(256) unsigned char g_chom_scratch[kNoAllocScratchBytes];
+
+// Device address of g_chom_scratch, looked up once per device.  In host code
+// the array's name is only a host-side stand-in, so kernels must be given this
+// address instead.
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_ptr[64];
+
+static int noalloc_scratch(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (dev < 0 || dev >= 64) return set_err(nullptr, SHL_EINVAL, "device ordinal %d out of range [0, 64)", dev);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_chom_scratch);
+        if (e != cudaSuccess || !p)
+            return set_err(nullptr, SHL_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SHL_OK;
+}
+
+}  // namespace shl
+
+extern "C" int shl_chom_noalloc(int32_t r, const uint8_t *mask_dev, const double *rho_dev, double E, double nu,
+                                double E_void, const double *u_dev, double *C_dev, void *stream) {
+    if (r < 1 || r > kNoAllocMaxR)
+        return set_err(nullptr, SHL_EINVAL, "shl_chom_noalloc: grid size r=%d outside [1, %d]", r, kNoAllocMaxR);
+    if (!u_dev || !C_dev || (!mask_dev && !rho_dev))
+        return set_err(nullptr, SHL_EINVAL, "shl_chom_noalloc: NULL buffer");
+    if (!(nu > -1.0 && nu < 0.5)) return set_err(nullptr, SHL_EINVAL, "Poisson ratio %g outside (-1, 0.5)", nu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_err(nullptr, SHL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    unsigned char *scratch = nullptr;
+    SHL_TRY(noalloc_scratch(dev, &scratch));
+    ElemOp<double> op;
+    SHL_TRY(get_op(nullptr, nu, r, &op));
+    const size_t N = (size_t)r * r * r;
+    const int g = grid1d(N, kChomThreads, kNoAllocMaxBlocks);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ChomArgs a{};
+    a.r = r;
+    a.N = N;
+    a.u = u_dev;
+    a.mask = mask_dev;
+    a.rho = rho_dev;
+    a.E = E;
+    a.Evoid = E_void;
+    a.ticket = reinterpret_cast<unsigned *>(scratch);
+    a.partial = reinterpret_cast<double *>(scratch + 256);
+    a.C = C_dev;
+    a.op = op;
+    // the ticket must start at zero; the partials are fully overwritten
+    SHL_CUDA(nullptr, cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s));
+    const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
+    SHL_CUDA(nullptr, cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    chom_kernel<<<g, kChomThreads, smem, s>>>(a);
+    SHL_CUDA(nullptr, cudaGetLastError());
+    return SHL_OK;
+}

@@ -79,6 +79,8 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(shl_solve_opts), _dp,
                                             ctypes.POINTER(shl_stats), _vp]),
     "shl_get_counters": (ctypes.c_int, [_vp, ctypes.c_void_p]),
+    "shl_chom_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -232,6 +234,13 @@ def shl_homogenize_batch(ctx, designs: Sequence, rs: Sequence[int], opts: shl_so
                                     _stream(stream))
     _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
     return C.reshape(-1, 6, 6), [s.as_dict() for s in st]
+
+
+def shl_chom_noalloc(r: int, u, C_dev, mask=None, rho=None, E=1.0, nu=0.3, E_void=1e-6, stream=None):
+    """C^H into the 36-double device tensor C_dev without any device allocation
+    by the library (for callers that cannot allocate); see include/shl.h."""
+    _check(None, lib().shl_chom_noalloc(r, _ptr(mask), _ptr(rho), E, nu, E_void, _ptr(u), _ptr(C_dev),
+                                        _stream(stream)))
 
 
 class shl_counters(ctypes.Structure):
