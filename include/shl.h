@@ -107,12 +107,14 @@ typedef struct {
  *   precision      SHL_FP64: PCG entirely in FP64, restarted from the true
  *                  residual until it meets tol.
  *                  SHL_FP32_REFINE: FP32 stiffness apply and vectors with
- *                  FP64-class dot accumulation inside; outer FP64 residual
- *                  f - K x and FP64 correction until tol.
+ *                  FP64-class dot accumulation; the iterate is kept in FP64
+ *                  and the FP32 residual is replaced by the true FP64
+ *                  residual f - K x ("reliable update") whenever it has
+ *                  fallen by inner_tol, until the FP64 residual meets tol.
  *   density        SHL_MASK: binary rho; SHL_SMOOTH: rho = 1/(1+exp(-kappa(t-d)))
  *   kappa          logistic sharpness; <= 0 selects ln(9) * r (two-voxel rise)
- *   inner_tol      FP32_REFINE: relative reduction asked of each inner solve
- *                  (<= 0 selects 1e-5)
+ *   inner_tol      FP32_REFINE: residual reduction between reliable updates
+ *                  (<= 0 selects 1e-2)
  *   warm_start     use the displacements passed in (shl_solve) or kept for the
  *                  session (serving) as the initial guess
  */
@@ -131,7 +133,7 @@ typedef struct {
 typedef struct {
     int32_t iters[6];      /* CG iterations per load case (summed over restarts)    */
     double relres[6];      /* final ||f - K u|| / ||f|| per load case, FP64         */
-    int32_t n_refine;      /* restarts (FP64) or refinement steps (FP32_REFINE)    */
+    int32_t n_refine;      /* restarts (FP64) or reliable updates (FP32_REFINE)   */
     int32_t status;        /* shl_status of this result                            */
     double t;              /* half-thickness used                                  */
     double margin;         /* half gap around t when t was chosen from vf          */

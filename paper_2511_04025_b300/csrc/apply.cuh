@@ -56,169 +56,283 @@ struct ApplyArgs {
     double *dot_out;       // 6 sums (may be null)
     PcgState *st;          // PCG mode: active flags in, alpha = rz / pq out
     const int *active_in;  // per load-case flags when st == null (may be null)
+    int vec_ok;            // p is 16-byte aligned and r is a multiple of 16 / sizeof(T)
     ElemOp<T> op;
 };
 
-template <int TX, int TY>
-struct ApplyShape {
-    static constexpr int EX = TX + 1, EY = TY + 1, NX = TX + 2, NY = TY + 2;
-    static constexpr int NT = EX * EY;
-    static constexpr int PL = NX * NY;
-    static constexpr int THREADS = (NT + 31) / 32 * 32;
-    template <typename T>
-    static constexpr size_t smem() {
-        return sizeof(T) * (2 * 18 * PL + 2 * 18 * NT);
-    }
-};
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async; completion by group)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(ApplyShape<TX, TY>::THREADS) apply_kernel(const ApplyArgs<T> a) {
-    using S = ApplyShape<TX, TY>;
-    constexpr int EX = S::EX, NX = S::NX, NT = S::NT, PL = S::PL;
+struct ApplyShape {
+    static constexpr int EX = TX + 1, EY = TY + 1;  // element columns (one halo column towards -x, -y)
+    static constexpr int NT = EX * EY;
+    static constexpr int THREADS = (NT + 31) / 32 * 32;
+    static constexpr int VEC = 16 / sizeof(T);      // elements per 16-byte chunk
+    static constexpr int OFF = VEC - 1;             // shared position of node column lx = 0
+    static constexpr int PITCH = TX + 2 * VEC;      // row pitch: interior lx = 1.. starts 16-byte aligned
+    static constexpr int NY = TY + 2;
+    static constexpr int PLANE = 3 * NY * PITCH;    // one node plane, three components
+    static constexpr size_t smem() { return sizeof(T) * (2 * PLANE + 2 * 9 * NT); }
+};
+
+__host__ __device__ inline int wrap_near(int v, int r) { return v < 0 ? v + r : (v >= r ? v - r : v); }
+
+// One CTA = one load case k (blockIdx.z) x a TX x TY column tile (blockIdx.x)
+// x tz node planes (blockIdx.y).  Per z step: wait for the prefetched node
+// plane, start the copy of the next one (cp.async, 16-byte chunks for the
+// tile interior, wrapped scalars for the halo), transform the element's top
+// face (x, y butterflies), combine with the bottom face kept from the
+// previous step (z butterfly), apply the 3x3 blocks, split the result into
+// bottom/top faces, add the bottom face to the carried top face of the
+// element below, untransform and hand the three foreign corners of the node
+// plane to the +x / +y / +xy neighbours.
+template <typename T, int TX, int TY, bool RESID>
+__global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4 ? 2 : 1)
+    apply_kernel(const ApplyArgs<T> a) {
+    using S = ApplyShape<T, TX, TY>;
+    constexpr int EX = S::EX, NT = S::NT, PITCH = S::PITCH, NY = S::NY, PLANE = S::PLANE, OFF = S::OFF,
+                  VEC = S::VEC;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sp = reinterpret_cast<T *>(smraw);  // [2][18][PL] node planes
-    T *sx = sp + 2 * 18 * PL;              // [2][18][NT] corner exchange
+    T *sp = reinterpret_cast<T *>(smraw);  // [2][3][NY][PITCH] node planes
+    T *sx = sp + 2 * PLANE;                // [2][9][NT] corner exchange
 
     if (a.st && a.st->nactive == 0) return;  // uniform: the solve has finished
     const int r = a.r;
     const size_t N = a.N;
-    const int tid = threadIdx.x;
-    const bool el = tid < NT;
-    const int exl = el ? tid % EX : 0, eyl = el ? tid / EX : 0;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * a.tz;
-    const int ex = wrapi(x0 - 1 + exl, r), ey = wrapi(y0 - 1 + eyl, r);
-    const int nx = x0 - 1 + exl, ny = y0 - 1 + eyl;
-    const bool out_col = el && exl >= 1 && eyl >= 1 && nx < r && ny < r;
+    const int k = blockIdx.z;
+    bool act = k < a.nvec;
+    if (act && a.st) act = a.st->active[k] != 0;
+    if (act && a.active_in) act = a.active_in[k] != 0;
+    DotAcc<T> dacc;
 
-    bool act[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        bool on = k < a.nvec;
-        if (on && a.st) on = a.st->active[k] != 0;
-        if (on && a.active_in) on = a.active_in[k] != 0;
-        act[k] = on;
-    }
+    if (act) {
+        const int tid = threadIdx.x;
+        const bool el = tid < NT;
+        const int exl = el ? tid % EX : 0, eyl = el ? tid / EX : 0;
+        const int tiles_x = (r + TX - 1) / TX;
+        const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY, z0 = blockIdx.y * a.tz;
+        const int ex = wrapi(x0 - 1 + exl, r), ey = wrapi(y0 - 1 + eyl, r);
+        const int nx = x0 - 1 + exl, ny = y0 - 1 + eyl;
+        const bool out_col = el && exl >= 1 && eyl >= 1 && nx < r && ny < r;
+        const bool vec_ok = a.vec_ok && (x0 + TX <= r);
+        const T *pk = a.p + (size_t)(3 * k) * N;
+        const size_t rr = (size_t)r * r;
 
-    T acc_hi[6][3];
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) acc_hi[k][i] = T(0);
-    DotAcc<T> dacc[6];
+        auto load_plane = [&](int z, int slot) {
+            const T *base = pk + (size_t)wrapi(z, r) * rr;
+            T *dst = sp + slot * PLANE;
+            if (vec_ok) {
+                constexpr int NCH = TX / VEC + 2;
+                for (int idx = tid; idx < 3 * NY * NCH; idx += S::THREADS) {
+                    const int c = idx / (NY * NCH), rem = idx - c * (NY * NCH);
+                    const int ly = rem / NCH, ch = rem - ly * NCH;
+                    const int gy = wrapi(y0 - 1 + ly, r);
+                    const T *row = base + (size_t)c * N + (size_t)gy * r;
+                    T *drow = dst + (c * NY + ly) * PITCH + OFF;
+                    if (ch == 0)
+                        cp_async_small<sizeof(T)>(drow, row + wrap_near(x0 - 1, r));
+                    else if (ch == NCH - 1)
+                        cp_async_small<sizeof(T)>(drow + TX + 1, row + wrap_near(x0 + TX, r));
+                    else
+                        cp_async16(drow + 1 + (ch - 1) * VEC, row + x0 + (ch - 1) * VEC);
+                }
+            } else {
+                constexpr int NXX = TX + 2;
+                for (int idx = tid; idx < 3 * NY * NXX; idx += S::THREADS) {
+                    const int c = idx / (NY * NXX), rem = idx - c * (NY * NXX);
+                    const int ly = rem / NXX, lx = rem - ly * NXX;
+                    const T *src = base + (size_t)c * N + (size_t)wrapi(y0 - 1 + ly, r) * r + wrapi(x0 - 1 + lx, r);
+                    cp_async_small<sizeof(T)>(dst + (c * NY + ly) * PITCH + OFF + lx, src);
+                }
+            }
+            cp_async_commit();
+        };
 
-    auto load_plane = [&](int z, int slot) {
-        const int zw = wrapi(z, r);
-        const int total = 3 * a.nvec * PL;
-        for (int idx = tid; idx < total; idx += blockDim.x) {
-            const int c = idx / PL, rem = idx - c * PL;
-            if (!act[c / 3]) continue;
-            const int ly = rem / NX, lx = rem - ly * NX;
-            const int gx = wrapi(x0 - 1 + lx, r), gy = wrapi(y0 - 1 + ly, r);
-            sp[(slot * 18 + c) * PL + rem] = a.p[(size_t)c * N + ((size_t)zw * r + gy) * r + gx];
+        // top face of node plane in `slot`: x, y butterflies; also the raw own-node value
+        auto face = [&](int slot, T (&ft)[3][4], T (&own)[3]) {
+            const T *s = sp + slot * PLANE;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T *row0 = s + (c * NY + eyl) * PITCH + OFF + exl;
+                const T *row1 = row0 + PITCH;
+                const T a00 = row0[0], a10 = row0[1], a01 = row1[0], a11 = row1[1];
+                own[c] = a00;
+                const T s0 = a00 + a10, d0 = a00 - a10, s1 = a01 + a11, d1 = a01 - a11;
+                ft[c][0] = s0 + s1;
+                ft[c][1] = d0 + d1;
+                ft[c][2] = s0 - s1;
+                ft[c][3] = d0 - d1;
+            }
+        };
+
+        // Residual mode: H chi^k of the element-local test displacement.  chi^k
+        // is linear (chi_i = sum_d eps_id X_d, X on [0,h]^3), so only the
+        // constant mode (4 h sum_d eps_id) and the three linear modes m = 2^d
+        // (-4 h eps_id) are non-zero.
+        T ch0[3], chd[3][3];
+        if (RESID) {
+            const T h4 = T(4) / T(r);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                T sum = T(0);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const bool diag = (k < 3) && (i == k) && (d == k);
+                    const bool shear = (k >= 3) && (i != d) && (i != k - 3) && (d != k - 3);
+                    const T eps = diag ? T(1) : (shear ? T(0.5) : T(0));
+                    chd[i][d] = -h4 * eps;
+                    sum += eps;
+                }
+                ch0[i] = h4 * sum;
+            }
         }
-    };
 
-    load_plane(z0 - 1, 0);
-    for (int s = 0; s <= a.tz; ++s) {
-        const int ez = z0 - 1 + s;
-        if (ez >= r) break;  // uniform across the block
-        load_plane(ez + 1, (s + 1) & 1);
-        __syncthreads();
-        const int slo = s & 1, shi = (s + 1) & 1;
-        const bool out_plane = (s >= 1);
-        T Ee = T(0);
-        if (el) {
+        auto modulus = [&](int ez) -> T {
+            if (!el) return T(0);
             const size_t e = ((size_t)wrapi(ez, r) * r + ey) * r + ex;
-            Ee = a.rho ? (T)(a.Evoid + a.rho[e] * (a.E - a.Evoid)) : (a.mask[e] ? a.E : a.Evoid);
-            if (a.resid) Ee = -Ee;
+            T Ee = a.rho ? (T)(a.Evoid + a.rho[e] * (a.E - a.Evoid)) : (a.mask[e] ? a.E : a.Evoid);
+            return RESID ? -Ee : Ee;
+        };
+
+        T ftb[3][4], carry[3][4], own_b[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            own_b[c] = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) carry[c][j] = T(0);
         }
-        int kb = 0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            if (!act[k]) continue;
-            T w[3][8];
-            T *xb = sx + kb * 18 * NT;
-            if (el) {
-                T v[3][8];
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const int sl = (b & 4) ? shi : slo;
-                    const int li = (eyl + ((b >> 1) & 1)) * NX + exl + (b & 1);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) v[i][b] = sp[(sl * 18 + 3 * k + i) * PL + li];
-                }
-#pragma unroll
-                for (int i = 0; i < 3; ++i) wht8(v[i]);
-                if (a.resid) {
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) v[i][m] += a.op.chihat[k][i][m];
-                }
-                block_apply(a.op, v, w, Ee);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) wht8(w[i]);
-                // corners (1,0,0),(0,1,0),(1,1,0),(1,0,1),(0,1,1),(1,1,1) -> exchange
-                constexpr int cor[6] = {1, 2, 3, 5, 6, 7};
-#pragma unroll
-                for (int j = 0; j < 6; ++j)
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) xb[(j * 3 + i) * NT + tid] = w[i][cor[j]];
-            }
-            __syncthreads();
-            if (out_col) {
-                const int tl = tid - 1, td = tid - EX, tdl = tid - EX - 1;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const T lo = w[i][0] + xb[(0 * 3 + i) * NT + tl] + xb[(1 * 3 + i) * NT + td] +
-                                 xb[(2 * 3 + i) * NT + tdl];
-                    const T hi = w[i][4] + xb[(3 * 3 + i) * NT + tl] + xb[(4 * 3 + i) * NT + td] +
-                                 xb[(5 * 3 + i) * NT + tdl];
-                    if (out_plane) {
-                        const size_t n = ((size_t)ez * r + ny) * r + nx;
-                        T qv = acc_hi[k][i] + lo;
-                        if (a.pin && n == 0) qv = T(0);
-                        a.q[(size_t)(3 * k + i) * N + n] = qv;
-                        if (a.dot == 1)
-                            dacc[k].add(qv * sp[(slo * 18 + 3 * k + i) * PL + eyl * NX + exl]);
-                        else if (a.dot == 2)
-                            dacc[k].add(qv * qv);
-                    }
-                    acc_hi[k][i] = hi;
-                }
-            }
-            kb ^= 1;
-        }
+        load_plane(z0 - 1, 0);
+        load_plane(z0, 1);
+        cp_async_wait_all();
         __syncthreads();
+        if (el) face(0, ftb, own_b);
+        T Ee = modulus(z0 - 1);
+
+        for (int s = 0; s <= a.tz; ++s) {
+            const int ez = z0 - 1 + s;  // element plane; node planes ez (bottom), ez + 1 (top)
+            if (ez >= r) break;          // uniform
+            if (s > 0) {
+                cp_async_wait_all();     // node plane ez + 1 has landed
+                __syncthreads();
+            }
+            const bool more = (s < a.tz) && (ez + 1 < r);
+            if (more) load_plane(ez + 2, s & 1);  // slot of node plane ez, already in registers
+            const T Ee_next = more ? modulus(ez + 1) : T(0);
+            T own_t[3];
+            T ftt[3][4];
+            T w[3][4];  // node-plane ez corner values (x, y butterflies undone)
+            if (el) {
+                face((s + 1) & 1, ftt, own_t);
+                T u[3][8], y[3][8];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        u[c][j] = ftb[c][j] + ftt[c][j];
+                        u[c][j + 4] = ftb[c][j] - ftt[c][j];
+                    }
+                if (RESID) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        u[c][0] += ch0[c];
+                        u[c][1] += chd[c][0];
+                        u[c][2] += chd[c][1];
+                        u[c][4] += chd[c][2];
+                    }
+                }
+                block_apply(a.op, u, y, Ee);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    T F[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        F[j] = carry[c][j] + (y[c][j] + y[c][j + 4]);
+                        carry[c][j] = y[c][j] - y[c][j + 4];
+                    }
+                    const T t0 = F[0] + F[1], t1 = F[0] - F[1], t2 = F[2] + F[3], t3 = F[2] - F[3];
+                    w[c][0] = t0 + t2;
+                    w[c][1] = t1 + t3;
+                    w[c][2] = t0 - t2;
+                    w[c][3] = t1 - t3;
+                    ftb[c][0] = ftt[c][0];
+                    ftb[c][1] = ftt[c][1];
+                    ftb[c][2] = ftt[c][2];
+                    ftb[c][3] = ftt[c][3];
+                }
+            }
+            if (s > 0) {
+                T *xb = sx + (s & 1) * 9 * NT;
+                if (el) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) xb[(j * 3 + c) * NT + tid] = w[c][j + 1];
+                }
+                __syncthreads();
+                if (out_col) {
+                    const int tl = tid - 1, td = tid - EX, tdl = tid - EX - 1;
+                    const size_t n = ((size_t)ez * r + ny) * r + nx;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        T qv = w[c][0] + xb[(0 * 3 + c) * NT + tl] + xb[(1 * 3 + c) * NT + td] +
+                               xb[(2 * 3 + c) * NT + tdl];
+                        if (a.pin && n == 0) qv = T(0);
+                        a.q[(size_t)(3 * k + c) * N + n] = qv;
+                        if (a.dot == 1)
+                            dacc.add(qv * own_b[c]);
+                        else if (a.dot == 2)
+                            dacc.add(qv * qv);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) own_b[c] = own_t[c];
+            Ee = Ee_next;
+        }
+        cp_async_wait_all();
     }
 
     if (!a.dot) return;
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     double dsum[6];
+    const double mine = dacc.get();
 #pragma unroll
-    for (int k = 0; k < 6; ++k) dsum[k] = dacc[k].get();
+    for (int kk = 0; kk < 6; ++kk) dsum[kk] = (kk == k) ? mine : 0.0;
     block_reduce_store<6>(dsum, a.partial, bid);
     if (!last_block_ticket(a.ticket, nblocks)) return;
     __shared__ double tot[6];
     sum_partials_ordered<6>(a.partial, nblocks, tot);
     if (threadIdx.x == 0) {
         if (a.dot_out)
-            for (int k = 0; k < 6; ++k) a.dot_out[k] = tot[k];
+            for (int kk = 0; kk < 6; ++kk) a.dot_out[kk] = tot[kk];
         if (a.st) {
-            for (int k = 0; k < 6; ++k) {
-                if (!act[k]) continue;
-                const double pq = tot[k];
+            for (int kk = 0; kk < 6; ++kk) {
+                if (!a.st->active[kk]) continue;
+                const double pq = tot[kk];
                 if (!(pq > 0.0) || !isfinite(pq)) {
                     a.st->numeric_err = 1;
-                    a.st->active[k] = 0;
-                    a.st->alpha[k] = 0.0;
+                    a.st->active[kk] = 0;
+                    a.st->alpha[kk] = 0.0;
                 } else {
-                    a.st->alpha[k] = a.st->rz[k] / pq;
+                    a.st->alpha[kk] = a.st->rz[kk] / pq;
                 }
             }
             int na = 0;
-            for (int k = 0; k < 6; ++k) na += a.st->active[k];
+            for (int kk = 0; kk < 6; ++kk) na += a.st->active[kk];
             a.st->nactive = na;
         }
     }

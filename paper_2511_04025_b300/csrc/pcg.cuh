@@ -160,6 +160,86 @@ __global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
     }
 }
 
+// ---- mixed precision: reliable updates -------------------------------------
+//
+// The FP32 PCG keeps its Krylov direction; every time its recurrence
+// residual has fallen by a factor delta (or claims convergence) the FP32
+// correction is folded into the FP64 iterate, the true residual f - K x64 is
+// recomputed in FP64, and the FP32 residual is replaced by it.  The search
+// direction p = z + beta p_prev is moved to the new residual,
+// p += D^-1 (r_new - r_old), so the next step is the CG step from the true
+// residual along the same conjugate direction.
+
+// x64 += x32 ; x32 = 0 for the load cases in mask
+__global__ void reliable_fold_kernel(size_t N, float *x32, double *x64, int mask) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 6; ++k) {
+            if (!((mask >> k) & 1)) continue;
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                x64[o] += (double)x32[o];
+                x32[o] = 0.0f;
+            }
+        }
+    }
+}
+
+// r_new = float(r64); p += D^-1 (r_new - r) (or p = D^-1 r_new for the load
+// cases in restart, whose last direction update was skipped because their
+// FP32 residual claimed convergence); r = r_new; rz, rr for mask.
+// Last block: a load case stays active unless its true FP64 residual
+// (rr_true, squared) meets tol2 * bnorm2 or its iteration budget is spent.
+__global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, int mask, int restart,
+                                       const double *rr_true) {
+    PcgState *st = a.st;
+    DotAcc<float> dacc[12];
+    const size_t N = a.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const float di = a.dinv[n];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!((mask >> k) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                const float rn = (float)r64[o];
+                if ((restart >> k) & 1)
+                    a.p[o] = di * rn;
+                else
+                    a.p[o] += di * (rn - a.r[o]);
+                a.r[o] = rn;
+                dacc[k].add(rn * (di * rn));
+                dacc[6 + k].add(rn * rn);
+            }
+        }
+    }
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = dacc[k].get();
+    const unsigned nb = gridDim.x;
+    block_reduce_store<12>(acc, a.partial, blockIdx.x);
+    if (!last_block_ticket(&st->ticket_aux, nb)) return;
+    __shared__ double tot[12];
+    sum_partials_ordered<12>(a.partial, nb, tot);
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int k = 0; k < 6; ++k) {
+            if ((mask >> k) & 1) {
+                st->rz[k] = tot[k];
+                st->rr[k] = tot[6 + k];
+                if (!isfinite(rr_true[k]) || !isfinite(tot[k])) {
+                    st->numeric_err = 1;
+                    st->active[k] = 0;
+                } else {
+                    st->active[k] = (rr_true[k] > st->tol2 * st->bnorm2[k]) && (st->iters[k] < st->maxit);
+                }
+            }
+            na += st->active[k];
+        }
+        st->nactive = na;
+    }
+}
+
 // ---- refinement helpers ----------------------------------------------------
 
 // b32 = r64 / s_k for the load cases in mask (s_k = ||r64_k||), x32 = 0.

@@ -11,7 +11,6 @@ using namespace shl;
 namespace shl {
 
 constexpr int kTX = 16, kTY = 16;
-using Shape = ApplyShape<kTX, kTY>;
 
 inline int grid1d(size_t n, int threads = kBlk, int cap = 148 * 8) {
     size_t b = (n + threads - 1) / threads;
@@ -24,28 +23,31 @@ template <typename T>
 void apply_smem_attr() {
     static bool done = false;
     if (!done) {
-        cudaFuncSetAttribute(apply_kernel<T, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Shape::smem<T>());
+        cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ApplyShape<T, kTX, kTY>::smem());
+        cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ApplyShape<T, kTX, kTY>::smem());
         done = true;
     }
 }
 
 // z-extent of a CTA's tile: long enough to amortise the halo plane, short
 // enough to give two CTAs per SM at the grid sizes in use.
-inline int pick_tz(int r) {
-    const int nxy = ((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY);
+inline int pick_tz(int r, int nvec) {
+    const size_t nxy = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * nvec;
     int tz = 16;
-    while (tz > 4 && (size_t)nxy * ((r + tz - 1) / tz) < 2 * 148) tz >>= 1;
+    while (tz > 4 && nxy * ((r + tz - 1) / tz) < 2 * 148) tz >>= 1;
     return tz;
 }
 
-inline dim3 apply_grid(int r, int tz) { return dim3((r + kTX - 1) / kTX, (r + kTY - 1) / kTY, (r + tz - 1) / tz); }
-
 template <typename T>
 int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
+    using S = ApplyShape<T, kTX, kTY>;
     apply_smem_attr<T>();
-    a.tz = pick_tz(a.r);
-    const dim3 g = apply_grid(a.r, a.tz);
+    a.tz = pick_tz(a.r, a.nvec);
+    const int tiles = ((a.r + kTX - 1) / kTX) * ((a.r + kTY - 1) / kTY);
+    const dim3 g(tiles, (a.r + a.tz - 1) / a.tz, a.nvec);
+    a.vec_ok = (a.r % S::VEC == 0) && ((reinterpret_cast<uintptr_t>(a.p) & 15) == 0);
     if (a.dot) {
         if (!a.partial) {
             double *partial = nullptr;
@@ -58,7 +60,10 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
             a.ticket = ticket;
         }
     }
-    apply_kernel<T, kTX, kTY><<<g, Shape::THREADS, Shape::smem<T>(), s>>>(a);
+    if (a.resid)
+        apply_kernel<T, kTX, kTY, true><<<g, S::THREADS, S::smem(), s>>>(a);
+    else
+        apply_kernel<T, kTX, kTY, false><<<g, S::THREADS, S::smem(), s>>>(a);
     ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
@@ -399,45 +404,89 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         ++ctx->launches;
         PcgState *st = nullptr;
         SHL_TRY(ws_get_t(ctx, "pcg_state32", 1, &st));
-        double *scale = nullptr;
-        SHL_TRY(ws_get_t(ctx, "refine_scale", 8, &scale));
-        const double itol = o->inner_tol > 0.0 ? o->inner_tol : 1e-5;
-        const int max_outer = 40;
-        int outer = 0;
-        for (;; ++outer) {
-            SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
-            SHL_CUDA(ctx, cudaMemcpyAsync(hp.v, norms + 12, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            SHL_CUDA(ctx, cudaStreamSynchronize(s));
-            int want = 0;
-            double sc[8] = {1, 1, 1, 1, 1, 1, 1, 1};
-            for (int k = 0; k < 6; ++k) {
-                if (!std::isfinite(hp.v[k])) {
+        double *one = nullptr;
+        SHL_TRY(ws_get_t(ctx, "refine_scale", 8, &one));
+        const double h_one[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+        SHL_CUDA(ctx, cudaMemcpyAsync(one, h_one, sizeof(h_one), cudaMemcpyHostToDevice, s));
+        const double delta = o->inner_tol > 0.0 ? o->inner_tol : 1e-2;
+        // r64 = f - K x64 (pinned); r32 = float(r64); x32 = 0
+        SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+        refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, one, 0x3f, b.r, b.x);
+        ++ctx->launches;
+        pcg_config_kernel<<<1, 32, 0, s>>>(st, tol * tol, maxit, 1);
+        ++ctx->launches;
+        SHL_CUDA(ctx, cudaMemcpyAsync(st->bnorm2, norms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SHL_CUDA(ctx, cudaMemcpyAsync(hp.v, norms + 12, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SHL_CUDA(ctx, cudaStreamSynchronize(s));
+        double last_rr[6];
+        for (int k = 0; k < 6; ++k) last_rr[k] = hp.v[k];
+        // PCG with reliable updates (one pcg_run per interval between updates)
+        const double *rr_true = norms + 12;
+        int want = 0;
+        for (int k = 0; k < 6; ++k)
+            if (fpin[k] > 0.0 && last_rr[k] > tol * tol * fpin[k]) want |= 1 << k;
+        int updates = 0;
+        if (want) {
+            const size_t gv = grid1d(N, kBlk, 148 * 4);
+            double *partial = nullptr;
+            SHL_TRY(ws_get_t(ctx, "pcg_partial", (size_t)gv * 12, &partial));
+            VecArgs<float> va{N, b.x, b.r, b.p, b.q, b.dinv, st, partial};
+            pcg_init_kernel<float><<<gv, kBlk, 0, s>>>(va, want, 0);
+            ++ctx->launches;
+            ApplyArgs<float> a = make_apply<float>(r, den, op32);
+            a.p = b.p;
+            a.q = b.q;
+            a.pin = 1;
+            a.dot = 1;
+            a.st = st;
+            a.ticket = &st->ticket_apply;
+            const int chunk = 32;
+            PcgState hst;
+            for (long long it = 0;; it += chunk) {
+                if (it > (long long)maxit + 2 * chunk)
+                    return set_err(ctx, SHL_ENOCONV, "PCG did not stop within %d iterations", maxit);
+                for (int c = 0; c < chunk; ++c) {
+                    SHL_TRY(launch_apply<float>(ctx, a, s));
+                    pcg_update_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                    pcg_direction_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                    ctx->launches += 2;
+                }
+                SHL_CUDA(ctx, cudaGetLastError());
+                SHL_CUDA(ctx, cudaMemcpyAsync(&hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+                SHL_CUDA(ctx, cudaStreamSynchronize(s));
+                if (hst.numeric_err) {
                     out->status = SHL_ENUMERIC;
-                    continue;
+                    break;
                 }
-                if (fpin[k] > 0.0 && hp.v[k] > tol * tol * fpin[k] && total_it[k] < maxit) {
-                    want |= 1 << k;
-                    sc[k] = std::sqrt(hp.v[k]);
+                // want: load cases not yet verified converged by their FP64 residual
+                int mask = 0, restart = 0;
+                for (int k = 0; k < 6; ++k)
+                    if ((want >> k) & 1) {
+                        const bool stopped = !hst.active[k];
+                        if (stopped || hst.rr[k] <= delta * delta * last_rr[k]) mask |= 1 << k;
+                        if (stopped) restart |= 1 << k;
+                    }
+                if (mask) {
+                    ++updates;
+                    reliable_fold_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, x64, mask);
+                    ++ctx->launches;
+                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+                    reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, r64, mask, restart, rr_true);
+                    ++ctx->launches;
+                    SHL_CUDA(ctx, cudaMemcpyAsync(&hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+                    SHL_CUDA(ctx, cudaMemcpyAsync(hp.v, norms + 12, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+                    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+                    for (int k = 0; k < 6; ++k)
+                        if ((mask >> k) & 1) {
+                            last_rr[k] = hp.v[k];
+                            if (!hst.active[k]) want &= ~(1 << k);  // converged (or out of iterations)
+                        }
                 }
+                if (hst.nactive == 0 && !want) break;
             }
-            if (!want || outer >= max_outer || out->status == SHL_ENUMERIC) break;
-            SHL_CUDA(ctx, cudaMemcpyAsync(scale, sc, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
-            refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, scale, want, b.r, b.x);
-            ++ctx->launches;
-            pcg_config_kernel<<<1, 32, 0, s>>>(st, itol * itol, maxit, 1);
-            ++ctx->launches;
-            SHL_TRY(pcg_run<float>(ctx, r, den, op32, b, st, want, 1, s, hp.nactive, maxit));
-            refine_gather_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, scale, want, x64);
-            ++ctx->launches;
-            int its[6], nerr = 0;
-            SHL_CUDA(ctx, cudaMemcpyAsync(its, st->iters, sizeof(its), cudaMemcpyDeviceToHost, s));
-            SHL_CUDA(ctx, cudaMemcpyAsync(&nerr, &st->numeric_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-            SHL_CUDA(ctx, cudaStreamSynchronize(s));
-            if (nerr) out->status = SHL_ENUMERIC;
-            for (int k = 0; k < 6; ++k)
-                if ((want >> k) & 1) total_it[k] += its[k];
+            for (int k = 0; k < 6; ++k) total_it[k] = hst.iters[k];
         }
-        out->n_refine = outer;
+        out->n_refine = updates;
     } else {
         return set_err(ctx, SHL_EINVAL, "unknown precision mode %d", o->precision);
     }
@@ -518,7 +567,7 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->precision = SHL_FP64;
     o->density = SHL_MASK;
     o->kappa = 0.0;
-    o->inner_tol = 1e-5;
+    o->inner_tol = 1e-2;
 }
 
 int shl_create(const shl_opts *opts, shl_ctx **out) {

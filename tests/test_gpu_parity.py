@@ -192,6 +192,19 @@ def test_homogenize_fp32_refine_matches_oracle(ctx, name, seed):
     assert entry_err(C, g["C"]) <= 1e-9  # refinement restores the FP64 level
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32r", 1e-4), ("fp64", 1e-9)])
+def test_homogenize_gaussian64_matches_oracle(ctx, prec, tol):
+    """64^3, 32 charges with N(0,1) magnitudes, 8 % solid: both precision modes
+    against the oracle (solved to 1e-12)."""
+    g = gold("gaussian64_s0")
+    d = inputs.gaussian_64(0)
+    p = shl.SHL_FP32_REFINE if prec == "fp32r" else shl.SHL_FP64
+    C, st = shl.shl_homogenize(ctx, d, 64, shl.default_solve_opts(tol=1e-10, precision=p))
+    assert st["status"] == 0 and st["n_solid"] == g["n_solid"] and st["n_ambiguous"] == 0
+    assert max(st["relres"]) <= 1e-10
+    assert entry_err(C, g["C"]) <= tol
+
+
 def test_solid_cell_returns_base_tensor(ctx):
     r = 16
     m = torch.ones(r ** 3, dtype=torch.uint8, device=DEV)
