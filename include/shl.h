@@ -221,6 +221,55 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
                          double *C_out, shl_stats *st, void *stream);
 
+/*
+ * Serving: continuous batching of homogenisation requests (the paper's
+ * interactive edit -> re-evaluate loop, Sec. 5.1, and the batches of designs
+ * an optimiser submits, Sec. 4.3).  Requests are copied at submit and queued
+ * FIFO; a pool of max_batch worker slots (each with its own stream and
+ * workspace) takes the head request as soon as a slot is free and its HBM
+ * footprint fits the budget, so requests that arrive while others run are
+ * admitted immediately and their kernels overlap on the GPU.  Each slot runs
+ * the same path as shl_homogenize, so a result is identical alone and in a
+ * mix.  With opts.warm_start and session >= 0, the session's last
+ * displacements (kept on the device, same r) seed the solve.
+ */
+typedef struct {
+    shl_design design;    /* copied at submit */
+    int32_t r;
+    shl_solve_opts opts;
+    int64_t session;      /* warm-start key, < 0 for none */
+} shl_request;
+
+typedef struct {
+    double C[36];
+    shl_stats stats;
+    double t_submit, t_admit, t_done;  /* seconds since the context was created */
+    int32_t warm;                      /* 1 if the solve started from a session's displacements */
+    int32_t slot;                      /* worker slot that ran it */
+} shl_result;
+
+typedef struct {
+    int32_t slots, queued, running;
+    uint64_t completed;
+    uint64_t held_bytes;    /* slot workspaces + warm-start cache */
+    uint64_t budget_bytes;
+} shl_serve_info;
+
+/* Non-blocking.  SHL_EINVAL (nothing queued) for an invalid request or one
+ * whose footprint can never fit the budget. */
+int shl_serve_submit(shl_ctx *ctx, const shl_request *req, uint64_t *ticket);
+/* SHL_EAGAIN while queued or running; on completion fills out (out->stats.status
+ * is the request's own status) and forgets the ticket; SHL_ENOTFOUND otherwise. */
+int shl_serve_poll(shl_ctx *ctx, uint64_t ticket, shl_result *out);
+/* Blocks until the request completes, then as shl_serve_poll. */
+int shl_serve_wait(shl_ctx *ctx, uint64_t ticket, shl_result *out);
+/* Removes a queued request (SHL_OK); SHL_EAGAIN if it is already running
+ * (it completes normally); SHL_ENOTFOUND for an unknown ticket. */
+int shl_serve_cancel(shl_ctx *ctx, uint64_t ticket);
+/* Blocks until nothing is queued or running. */
+int shl_serve_drain(shl_ctx *ctx);
+int shl_serve_info_get(shl_ctx *ctx, shl_serve_info *out);
+
 /* Telemetry of a context since creation: kernels launched by the library and
  * device workspace bytes currently held.  No device work. */
 typedef struct {

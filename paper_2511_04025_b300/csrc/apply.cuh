@@ -128,10 +128,12 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         const int nx = x0 - 1 + exl, ny = y0 - 1 + eyl;
         const bool out_col = el && exl >= 1 && eyl >= 1 && nx < r && ny < r;
         const bool vec_ok = a.vec_ok && (x0 + TX <= r);
-        const T *pk = a.p + (size_t)(3 * k) * N;
+        const bool zero_in = (a.p == nullptr);  // residual of x = 0 (the loads f)
+        const T *pk = zero_in ? nullptr : a.p + (size_t)(3 * k) * N;
         const size_t rr = (size_t)r * r;
 
         auto load_plane = [&](int z, int slot) {
+            if (zero_in) return;
             const T *base = pk + (size_t)wrapi(z, r) * rr;
             T *dst = sp + slot * PLANE;
             if (vec_ok) {
@@ -166,6 +168,10 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
             const T *s = sp + slot * PLANE;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
+                if (zero_in) {
+                    own[c] = ft[c][0] = ft[c][1] = ft[c][2] = ft[c][3] = T(0);
+                    continue;
+                }
                 const T *row0 = s + (c * NY + eyl) * PITCH + OFF + exl;
                 const T *row1 = row0 + PITCH;
                 const T a00 = row0[0], a10 = row0[1], a01 = row1[0], a11 = row1[1];

@@ -6,6 +6,8 @@
 #include "field.cuh"
 #include "pcg.cuh"
 
+#include <atomic>
+
 using namespace shl;
 
 namespace shl {
@@ -19,16 +21,20 @@ inline int grid1d(size_t n, int threads = kBlk, int cap = 148 * 8) {
     return (int)b;
 }
 
+// Dynamic shared-memory opt-in of the apply kernels, once per device
+// (thread-safe; setting it twice is harmless).
 template <typename T>
 void apply_smem_attr() {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ApplyShape<T, kTX, kTY>::smem());
-        cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ApplyShape<T, kTX, kTY>::smem());
-        done = true;
-    }
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ApplyShape<T, kTX, kTY>::smem());
+    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ApplyShape<T, kTX, kTY>::smem());
+    done.fetch_or(bit, std::memory_order_release);
 }
 
 // z-extent of a CTA's tile: long enough to amortise the halo plane, short
@@ -141,7 +147,7 @@ inline int run_select(shl_ctx *ctx, const double *dd, size_t n, double vf, cudaS
     if (k0 < 1) k0 = 1;
     if (k0 > (long long)n - 1) k0 = (long long)n - 1;
     const long long lo = std::max(1LL, k0 - kSelW), hi = std::min((long long)n, k0 + kSelW + 1);
-    static SelectState init;  // host staging (only the header part is copied)
+    static thread_local SelectState init;  // host staging (only the header part is copied)
     std::memset(&init, 0, offsetof(SelectState, buf));
     init.rank[0] = (unsigned long long)lo;
     init.rank[1] = (unsigned long long)hi;
@@ -303,7 +309,7 @@ struct SolveOut {
 };
 
 // Residual f - K x (FP64) with its squared norms per load case; pin selects
-// the pinned system.
+// the pinned system; x == nullptr means x = 0 (the loads f themselves).
 inline int resid64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double> &op, const double *x, double *out,
                    int pin, double *dot_out, cudaStream_t s) {
     ApplyArgs<double> a = make_apply<double>(r, den, op);
@@ -343,12 +349,9 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
     double *r64 = nullptr, *norms = nullptr;
     SHL_TRY(ws_get_t(ctx, "r64", NV, &r64));
     SHL_TRY(ws_get_t(ctx, "norms", 32, &norms));  // [0:6] |f|^2, [12:18] |f - K x|^2 (pinned system)
-    double *zero = nullptr;
-    SHL_TRY(ws_get_t(ctx, "zero64", NV, &zero));
-    SHL_CUDA(ctx, cudaMemsetAsync(zero, 0, NV * sizeof(double), s));
     if (!warm) SHL_CUDA(ctx, cudaMemsetAsync(x64, 0, NV * sizeof(double), s));
     // ||f||^2 of the pinned system (r64 = f afterwards)
-    SHL_TRY(resid64(ctx, r, den, op64, zero, r64, 1, norms + 0, s));
+    SHL_TRY(resid64(ctx, r, den, op64, nullptr, r64, 1, norms + 0, s));
     double fpin[6];
     SHL_CUDA(ctx, cudaMemcpyAsync(fpin, norms, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
@@ -549,6 +552,104 @@ inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
     return SHL_OK;
 }
 
+// Solve + C^H for a given density on stream s (caller validated the arguments
+// and holds the context lock).  u_dev: displacements (in: initial guess when
+// warm; out: solution), or null for a context workspace.
+inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double *rho_dev, const shl_solve_opts *o,
+                      double *u_dev, bool warm, double *C_out, shl_stats *st, cudaStream_t s) {
+    const size_t NV = (size_t)18 * r * r * r;
+    double *x64 = u_dev;
+    if (!x64) SHL_TRY(ws_get_t(ctx, "x64", NV, &x64));
+    Density den{mask_dev, rho_dev, o->E, o->E_void};
+    SolveOut so;
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventRecord(e0, s);
+    int rc = run_solve(ctx, r, den, o, x64, warm, s, &so);
+    cudaEventRecord(e1, s);
+    double *Cd = nullptr;
+    if (rc == SHL_OK) rc = ws_get_t(ctx, "chom_out", 36, &Cd);
+    if (rc == SHL_OK) rc = run_chom(ctx, r, den, o->nu, x64, Cd, s);
+    cudaEventRecord(e2, s);
+    if (rc == SHL_OK && C_out) cudaMemcpyAsync(C_out, Cd, 36 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (st) {
+        for (int k = 0; k < 6; ++k) {
+            st->iters[k] = so.iters[k];
+            st->relres[k] = so.relres[k];
+        }
+        st->n_refine = so.n_refine;
+        st->status = rc != SHL_OK ? rc : so.status;
+        cudaEventElapsedTime(&st->ms_solve, e0, e1);
+        cudaEventElapsedTime(&st->ms_chom, e1, e2);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (rc != SHL_OK) return rc;
+    if (so.status == SHL_ENUMERIC) return set_err(ctx, SHL_ENUMERIC, "NaN/Inf in the solve");
+    if (so.status == SHL_ENOCONV) return set_err(ctx, SHL_ENOCONV, "a load case did not reach tol");
+    return SHL_OK;
+}
+
+// The whole path for one design on stream s (arguments validated, lock held).
+inline int homogenize_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_opts *o, double *C_out,
+                           shl_stats *st, cudaStream_t s, double *x64, bool warm) {
+    uint8_t *mask = nullptr;
+    double *rho = nullptr;
+    const size_t N = (size_t)r * r * r;
+    SHL_TRY(ws_get_t(ctx, "hom_mask", N, &mask));
+    if (o->density == SHL_SMOOTH) SHL_TRY(ws_get_t(ctx, "hom_rho", N, &rho));
+    if (st) std::memset(st, 0, sizeof(*st));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    VoxOut v;
+    int rc = run_voxelize(ctx, d, r, o->kappa, mask, rho, nullptr, s, &v);
+    cudaEventRecord(e1, s);
+    if (rc == SHL_OK)
+        rc = solve_impl(ctx, r, o->density == SHL_SMOOTH ? nullptr : mask, rho, o, x64, warm, C_out, st, s);
+    if (st) {
+        cudaEventElapsedTime(&st->ms_field, e0, e1);
+        st->t = v.t;
+        st->margin = v.margin;
+        st->n_solid = v.n_solid;
+        st->n_ambiguous = v.n_amb;
+        if (rc != SHL_OK && st->status == SHL_OK) st->status = rc;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+// Device workspace bytes a design of grid r needs (admission estimate).
+inline size_t design_footprint(int r, const shl_solve_opts *o) {
+    const size_t N = (size_t)r * r * r;
+    size_t per = 144 + 144 + 8 + 1 + 8;  // x64, r64, distances, mask, dinv
+    per += (o->precision == SHL_FP64) ? 144 + 144 : 4 * 72;
+    if (o->density == SHL_SMOOTH) per += 8;
+    return N * per + ((size_t)8 << 20);
+}
+
+}  // namespace shl
+
+#include "serve.cuh"
+
+namespace shl {
+// serving slots count toward the owning context's telemetry
+inline void serve_counters(shl_ctx *ctx, shl_counters *out) {
+    auto *sv = static_cast<Server *>(ctx->serve);
+    if (!sv) return;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto *w : sv->slot_ctx) {
+        out->kernel_launches += w->launches;
+        out->workspace_bytes += ctx_ws_bytes(w);
+    }
+    out->workspace_bytes += sv->warm_bytes;
+}
 }  // namespace shl
 
 // ===========================================================================
@@ -598,6 +699,7 @@ int shl_create(const shl_opts *opts, shl_ctx **out) {
 int shl_destroy(shl_ctx *ctx) {
     if (!ctx) return SHL_OK;
     cudaSetDevice(ctx->device);
+    serve_stop(ctx);
     cudaStreamSynchronize(ctx->stream);
     ws_free_all(ctx);
     cudaStreamDestroy(ctx->stream);
@@ -707,43 +809,8 @@ int shl_solve(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rh
     if (r < 2 || r > 1024) return set_err(ctx, SHL_EINVAL, "grid size r=%d out of range [2, 1024]", r);
     if (!mask_dev && !rho_dev) return set_err(ctx, SHL_EINVAL, "no density given");
     cudaSetDevice(ctx->device);
-    cudaStream_t s = pick_stream(ctx, stream);
-    const size_t NV = (size_t)18 * r * r * r;
-    double *x64 = u_dev;
-    if (!x64) SHL_TRY(ws_get_t(ctx, "x64", NV, &x64));
-    Density den{mask_dev, rho_dev, o->E, o->E_void};
-    SolveOut so;
-    cudaEvent_t e0, e1, e2;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventCreate(&e2);
-    cudaEventRecord(e0, s);
-    int rc = run_solve(ctx, r, den, o, x64, o->warm_start && u_dev, s, &so);
-    cudaEventRecord(e1, s);
-    double *Cd = nullptr;
-    if (rc == SHL_OK) rc = ws_get_t(ctx, "chom_out", 36, &Cd);
-    if (rc == SHL_OK) rc = run_chom(ctx, r, den, o->nu, x64, Cd, s);
-    cudaEventRecord(e2, s);
-    if (rc == SHL_OK && C_out) cudaMemcpyAsync(C_out, Cd, 36 * sizeof(double), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    if (st) {
-        std::memset(st, 0, sizeof(*st));
-        for (int k = 0; k < 6; ++k) {
-            st->iters[k] = so.iters[k];
-            st->relres[k] = so.relres[k];
-        }
-        st->n_refine = so.n_refine;
-        st->status = rc != SHL_OK ? rc : so.status;
-        cudaEventElapsedTime(&st->ms_solve, e0, e1);
-        cudaEventElapsedTime(&st->ms_chom, e1, e2);
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
-    if (rc != SHL_OK) return rc;
-    if (so.status == SHL_ENUMERIC) return set_err(ctx, SHL_ENUMERIC, "NaN/Inf in the solve");
-    if (so.status == SHL_ENOCONV) return set_err(ctx, SHL_ENOCONV, "a load case did not reach tol");
-    return SHL_OK;
+    if (st) std::memset(st, 0, sizeof(*st));
+    return solve_impl(ctx, r, mask_dev, rho_dev, o, u_dev, o->warm_start && u_dev, C_out, st, pick_stream(ctx, stream));
 }
 
 int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, double *C_out,
@@ -754,31 +821,7 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
     SHL_TRY(validate_design(ctx, d, r));
     if (!C_out) return set_err(ctx, SHL_EINVAL, "C_out is NULL");
     cudaSetDevice(ctx->device);
-    uint8_t *mask = nullptr;
-    double *rho = nullptr;
-    const size_t N = (size_t)r * r * r;
-    SHL_TRY(ws_get_t(ctx, "hom_mask", N, &mask));
-    if (o->density == SHL_SMOOTH) SHL_TRY(ws_get_t(ctx, "hom_rho", N, &rho));
-    cudaStream_t s = pick_stream(ctx, stream);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-    VoxOut v;
-    int rc = run_voxelize(ctx, d, r, o->kappa, mask, rho, nullptr, s, &v);
-    cudaEventRecord(e1, s);
-    if (rc == SHL_OK)
-        rc = shl_solve(ctx, r, o->density == SHL_SMOOTH ? nullptr : mask, rho, o, nullptr, C_out, st, s);
-    if (st) {
-        cudaEventElapsedTime(&st->ms_field, e0, e1);
-        st->t = v.t;
-        st->margin = v.margin;
-        st->n_solid = v.n_solid;
-        st->n_ambiguous = v.n_amb;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return rc;
+    return homogenize_impl(ctx, d, r, o, C_out, st, pick_stream(ctx, stream), nullptr, false);
 }
 
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
@@ -801,6 +844,7 @@ int shl_get_counters(shl_ctx *ctx, shl_counters *out) {
     uint64_t b = 0;
     for (auto &kv : ctx->ws.slots) b += kv.second.second;
     out->workspace_bytes = b;
+    serve_counters(ctx, out);
     return SHL_OK;
 }
 

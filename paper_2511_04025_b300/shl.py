@@ -56,6 +56,25 @@ class shl_stats(ctypes.Structure):
                     ms_field=self.ms_field, ms_solve=self.ms_solve, ms_chom=self.ms_chom)
 
 
+class shl_request(ctypes.Structure):
+    _fields_ = [("design", shl_design), ("r", ctypes.c_int32), ("opts", shl_solve_opts), ("session", ctypes.c_int64)]
+
+
+class shl_result(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_double * 36), ("stats", shl_stats), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("warm", ctypes.c_int32),
+                ("slot", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return dict(C=np.array(self.C).reshape(6, 6), stats=self.stats.as_dict(), t_submit=self.t_submit,
+                    t_admit=self.t_admit, t_done=self.t_done, warm=bool(self.warm), slot=self.slot)
+
+
+class shl_serve_info(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("queued", ctypes.c_int32), ("running", ctypes.c_int32),
+                ("completed", ctypes.c_uint64), ("held_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
+
+
 # Every symbol include/shl.h declares, with its ctypes signature.
 SIGNATURES = {
     "shl_create": (ctypes.c_int, [ctypes.POINTER(shl_opts), ctypes.POINTER(_vp)]),
@@ -81,6 +100,12 @@ SIGNATURES = {
     "shl_get_counters": (ctypes.c_int, [_vp, ctypes.c_void_p]),
     "shl_chom_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _vp, _vp, _vp]),
+    "shl_serve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(shl_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "shl_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(shl_result)]),
+    "shl_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(shl_result)]),
+    "shl_serve_cancel": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "shl_serve_drain": (ctypes.c_int, [_vp]),
+    "shl_serve_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(shl_serve_info)]),
 }
 
 _lib = None
@@ -241,6 +266,51 @@ def shl_chom_noalloc(r: int, u, C_dev, mask=None, rho=None, E=1.0, nu=0.3, E_voi
     by the library (for callers that cannot allocate); see include/shl.h."""
     _check(None, lib().shl_chom_noalloc(r, _ptr(mask), _ptr(rho), E, nu, E_void, _ptr(u), _ptr(C_dev),
                                         _stream(stream)))
+
+
+def shl_serve_submit(ctx, design, r: int, opts: shl_solve_opts, session: int = -1) -> int:
+    """Queue one design (copied at submit); returns its ticket."""
+    d = DesignArg(design)
+    req = shl_request(design=d.s, r=r, opts=opts, session=session)
+    t = ctypes.c_uint64()
+    _check(ctx, lib().shl_serve_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def shl_serve_poll(ctx, ticket: int) -> Optional[dict]:
+    """Result dict when the request has completed, None while it is pending."""
+    res = shl_result()
+    st = lib().shl_serve_poll(ctx, ticket, ctypes.byref(res))
+    if st == SHL_EAGAIN:
+        return None
+    _check(ctx, st)
+    return res.as_dict()
+
+
+def shl_serve_wait(ctx, ticket: int) -> dict:
+    res = shl_result()
+    _check(ctx, lib().shl_serve_wait(ctx, ticket, ctypes.byref(res)))
+    return res.as_dict()
+
+
+def shl_serve_cancel(ctx, ticket: int) -> bool:
+    """True if the request was removed from the queue, False if it was already running."""
+    st = lib().shl_serve_cancel(ctx, ticket)
+    if st == SHL_EAGAIN:
+        return False
+    _check(ctx, st)
+    return True
+
+
+def shl_serve_drain(ctx) -> None:
+    _check(ctx, lib().shl_serve_drain(ctx))
+
+
+def shl_serve_info_get(ctx) -> dict:
+    i = shl_serve_info()
+    _check(ctx, lib().shl_serve_info_get(ctx, ctypes.byref(i)))
+    return dict(slots=i.slots, queued=i.queued, running=i.running, completed=i.completed,
+                held_bytes=i.held_bytes, budget_bytes=i.budget_bytes)
 
 
 class shl_counters(ctypes.Structure):

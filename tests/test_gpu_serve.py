@@ -1,0 +1,95 @@
+"""Serving (continuous batching) through the C-ABI: a result is the same alone
+and in a mix, admission respects the HBM budget, warm starts converge from a
+session's previous displacements, queued requests can be cancelled."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_04025_b300 import inputs, shl  # noqa: E402
+
+
+def _opts(**kw):
+    return shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10, **kw)
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device: GPU tests need a B300")
+
+
+def test_result_alone_equals_result_in_mix(gpu):
+    probe = inputs.random_design(7, 16, 0.12)
+    with shl.Context(0, max_batch=6) as c:
+        t = shl.shl_serve_submit(c.handle, probe, 24, _opts())
+        alone = shl.shl_serve_wait(c.handle, t)
+        mix = [inputs.random_design(100 + i, 8 + 4 * i, 0.05 + 0.02 * i) for i in range(5)]
+        rs = [32, 24, 20, 32, 16]
+        tickets = [shl.shl_serve_submit(c.handle, d, r, _opts()) for d, r in zip(mix[:2], rs[:2])]
+        tp = shl.shl_serve_submit(c.handle, probe, 24, _opts())
+        tickets += [shl.shl_serve_submit(c.handle, d, r, _opts()) for d, r in zip(mix[2:], rs[2:])]
+        res = {tk: shl.shl_serve_wait(c.handle, tk) for tk in tickets + [tp]}
+        inmix = res[tp]
+        # the mix really overlapped on the GPU
+        spans = sorted((v["t_admit"], v["t_done"]) for v in res.values())
+        assert any(b[0] < a[1] for a, b in zip(spans, spans[1:]))
+        assert alone["stats"]["status"] == 0 and inmix["stats"]["status"] == 0
+        # same launch shapes and reduction orders -> bitwise the same result
+        assert np.array_equal(alone["C"], inmix["C"])
+        # and each mix member matches its own direct homogenisation
+        for d, r, tk in zip(mix[:2], rs[:2], tickets[:2]):
+            C, _ = shl.shl_homogenize(c.handle, d, r, _opts())
+            assert np.array_equal(C, res[tk]["C"])
+
+
+def test_admission_respects_small_budget(gpu):
+    d = inputs.random_design(3, 12, 0.1)
+    foot32 = 32 ** 3 * (144 + 144 + 8 + 1 + 8 + 4 * 72) + (8 << 20)
+    budget = int(1.5 * foot32)
+    with shl.Context(0, max_batch=4, hbm_budget_bytes=budget) as c:
+        ts = [shl.shl_serve_submit(c.handle, d.copy(pos=np.mod(d.pos + 0.01 * i, 1.0)), 32, _opts())
+              for i in range(4)]
+        res = [shl.shl_serve_wait(c.handle, t) for t in ts]
+        spans = sorted((v["t_admit"], v["t_done"]) for v in res)
+        for a, b in zip(spans, spans[1:]):
+            assert b[0] >= a[1]  # only one design fits at a time
+        info = shl.shl_serve_info_get(c.handle)
+        assert info["held_bytes"] <= budget and info["completed"] == 4
+        with pytest.raises(shl.ShlError) as e:
+            shl.shl_serve_submit(c.handle, d, 64, _opts())  # can never fit
+        assert e.value.status == shl.SHL_EINVAL
+
+
+def test_warm_start_from_session(gpu):
+    d = inputs.random_design(11, 16, 0.1)
+    d2 = d.copy(pos=np.mod(d.pos + np.random.default_rng(0).normal(0, 0.002, d.pos.shape), 1.0))
+    with shl.Context(0, max_batch=2) as c:
+        shl.shl_serve_wait(c.handle, shl.shl_serve_submit(c.handle, d, 32, _opts(warm_start=1), session=5))
+        cold = shl.shl_serve_wait(c.handle, shl.shl_serve_submit(c.handle, d2, 32, _opts(), session=-1))
+        warm = shl.shl_serve_wait(c.handle, shl.shl_serve_submit(c.handle, d2, 32, _opts(warm_start=1), session=5))
+        assert warm["warm"] and not cold["warm"]
+        assert warm["stats"]["status"] == 0 and max(warm["stats"]["relres"]) <= 1e-10
+        s = np.abs(cold["C"]).max()
+        assert np.max(np.abs(warm["C"] - cold["C"]) / np.maximum(np.abs(cold["C"]), 1e-2 * s)) <= 1e-8
+        assert sum(warm["stats"]["iters"]) < sum(cold["stats"]["iters"])
+
+
+def test_cancel_unknown_and_invalid(gpu):
+    d = inputs.random_design(1, 8, 0.1)
+    with shl.Context(0, max_batch=1) as c:
+        t1 = shl.shl_serve_submit(c.handle, d, 32, _opts())
+        t2 = shl.shl_serve_submit(c.handle, d, 32, _opts())
+        t3 = shl.shl_serve_submit(c.handle, d, 32, _opts())
+        assert shl.shl_serve_cancel(c.handle, t3) is True
+        shl.shl_serve_drain(c.handle)
+        assert shl.shl_serve_poll(c.handle, t1) is not None
+        assert shl.shl_serve_poll(c.handle, t2) is not None
+        for t in (t1, t3, 12345):
+            with pytest.raises(shl.ShlError) as e:
+                shl.shl_serve_poll(c.handle, t)
+            assert e.value.status == shl.SHL_ENOTFOUND
+        with pytest.raises(shl.ShlError) as e:
+            shl.shl_serve_submit(c.handle, d.copy(vf=None), 32, _opts())
+        assert e.value.status == shl.SHL_EINVAL
