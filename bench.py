@@ -174,6 +174,69 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving workload: a Poisson request stream (grids 32^3/64^3/96^3 at
+    0.50/0.35/0.15, 8-64 charges, 3-20 % solid, 25 % warm-start follow-ups).
+    Pass 1 submits everything at once (saturating burst) and measures the
+    closed-loop throughput X; pass 2 replays the stream with Poisson arrivals at
+    0.7 X.  Latency = submit -> result."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+
+    torch.cuda.set_device(0)
+    reqs = inputs.serving_stream(seed=0, n_requests=args.requests, rate_hz=1.0)
+    opts = lambda warm: shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10, warm_start=int(warm))
+
+    def replay(ctx, scale):
+        t0 = time.perf_counter()
+        tickets = []
+        for q in reqs:
+            if scale is not None:
+                wait = q.t_arrive * scale - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+            warm = q.follow_up_of >= 0
+            tickets.append((q, shl.shl_serve_submit(ctx.handle, q.design, q.r, opts(warm), session=q.session)))
+        out = [(q, shl.shl_serve_wait(ctx.handle, t)) for q, t in tickets]
+        wall = time.perf_counter() - t0
+        return wall, out
+
+    with shl.Context(0, max_batch=args.slots) as ctx:
+        # warm-up: one design per grid size
+        for r in (32, 64, 96):
+            shl.shl_serve_wait(ctx.handle, shl.shl_serve_submit(ctx.handle, reqs[0].design, r, opts(False)))
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk1:
+            wall1, res1 = replay(ctx, None)
+        X = len(reqs) / wall1
+        span = reqs[-1].t_arrive if reqs[-1].t_arrive > 0 else 1.0
+        scale = (len(reqs) / (0.7 * X)) / span  # seconds of replay per unit of stream time
+        c0 = shl.shl_get_counters(ctx.handle)["kernel_launches"]
+        with ClockSampler(0) as clk2:
+            wall2, res2 = replay(ctx, scale)
+        c1 = shl.shl_get_counters(ctx.handle)["kernel_launches"]
+
+    def lat(res, r=None):
+        v = [x["t_done"] - x["t_submit"] for q, x in res if r is None or q.r == r]
+        return (float(np.percentile(v, 50)), float(np.percentile(v, 99))) if v else (None, None)
+
+    ok = all(x["stats"]["status"] == 0 for _, x in res1 + res2)
+    p50, p99 = lat(res2)
+    p50_64, p99_64 = lat(res2, 64)
+    line = {
+        "metric": "served designs/sec (Poisson arrivals at 0.7x burst throughput)", "value": len(reqs) / wall2,
+        "unit": "designs/s", "n_gpus": 1, "steps": len(reqs), "warmup": 3, "ms_per_step": 1e3 * wall2 / len(reqs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "serve", "requests": len(reqs), "slots": args.slots, "grids": "32/64/96 @ .50/.35/.15",
+                   "tol": 1e-10, "warm_start_share": float(np.mean([q.follow_up_of >= 0 for q in reqs]))},
+        "latency_s": {"p50": p50, "p99": p99, "p50_64": p50_64, "p99_64": p99_64},
+        "burst": {"designs_per_s": X, "latency_p50": lat(res1)[0], "latency_p99": lat(res1)[1]},
+        "warm_hits": int(sum(1 for _, x in res2 if x["warm"])), "all_converged": ok,
+        "clocks": clk2.summary(), "gpu_launches": int(c1 - c0),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,9 +247,14 @@ def main():
     ap.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving workload (Poisson stream) instead of the bench")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
 
     import torch
     from paper_2511_04025_b300 import inputs, shl
