@@ -70,6 +70,8 @@ def lib():
                                 _dp, _dp, _dp]
         L.shlo_element_sensitivity.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                _dp, _dp, _dp]
+        L.shlo_field_vjp.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_long, _dp, _dp, _dp, _dp,
+                                     _dp]
         _lib = L
     return _lib
 
@@ -250,6 +252,51 @@ def element_sensitivity(r: int, u: np.ndarray, G: np.ndarray, E=1.0, nu=0.3, Evo
     G = np.ascontiguousarray(G, dtype=np.float64).ravel()
     assert lib().shlo_element_sensitivity(r, E, nu, Evoid, _p(np.ascontiguousarray(u)), _p(G), _p(g)) == 0
     return g
+
+
+def field_vjp(design, pts: np.ndarray, Fbar: np.ndarray, gFbar: np.ndarray):
+    """sum_p Fbar dF/dtheta + gFbar . d(grad F)/dtheta for theta = charge positions
+    (n x 3) and magnitudes (n) (chain rule through Eq. charge-field)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    g_pos = np.zeros((design.n, 3))
+    g_q = np.zeros(design.n)
+    alpha = None if design.alpha is None else np.ascontiguousarray(design.alpha, dtype=np.float64)
+    st = lib().shlo_field_vjp(design.n, _p(np.ascontiguousarray(design.pos, dtype=np.float64)),
+                              _p(np.ascontiguousarray(design.q, dtype=np.float64)), _p(alpha), design.K,
+                              pts.shape[0], _p(pts), _p(np.ascontiguousarray(Fbar, dtype=np.float64)),
+                              _p(np.ascontiguousarray(gFbar, dtype=np.float64)), _p(g_pos), _p(g_q))
+    assert st == 0
+    return g_pos, g_q
+
+
+def gradient(design, r: int, dEdC: np.ndarray, t: float, kappa: Optional[float] = None, E=1.0, nu=0.3,
+             Evoid=1e-6, tol=1e-12, maxit=200000):
+    """dE/dtheta through the smoothed density (Eq. chain), theta = charge
+    positions, magnitudes, iso-level c and half-thickness t, for an objective
+    with dE/dC^H = dEdC (6x6):
+      g_e        = dE/drho_e = sum_ij dEdC_ij (E - E_void) w_i^T Khat w_j  (self-adjoint cell problems)
+      dbeta/dd   = -kappa beta (1 - beta),   dbeta/dt = +kappa beta (1 - beta)
+      d          = |F - c| / |grad F|:  dd/dF = sgn(F - c)/|grad F|, dd/dc = -dd/dF,
+                   dd/d(grad F) = -|F - c| grad F / |grad F|^3
+    then back through F and grad F to the charges."""
+    F, gF = field_grid(design, r)
+    kap = default_kappa(r) if kappa is None else kappa
+    d = distance(F, gF, design.iso)
+    rho = beta(d, t, kap)
+    u, iters, relres, st = solve(r, rho, E, nu, Evoid, tol, maxit)
+    C, _ = chom(r, rho, u, E, nu, Evoid)
+    g_e = element_sensitivity(r, u, dEdC, E, nu, Evoid)
+    db = kap * rho * (1.0 - rho)            # dbeta/dt = -dbeta/dd
+    dE_dd = -g_e * db
+    gn = np.sqrt(np.sum(gF * gF, axis=1))
+    ok = gn > 0
+    Fbar = np.zeros_like(F)
+    gFbar = np.zeros_like(gF)
+    Fbar[ok] = dE_dd[ok] * np.sign(F[ok] - design.iso) / gn[ok]
+    gFbar[ok] = (dE_dd[ok] * (-np.abs(F[ok] - design.iso) / gn[ok] ** 3))[:, None] * gF[ok]
+    g_pos, g_q = field_vjp(design, voxel_centres(r), Fbar, gFbar)
+    return dict(C=C, g_pos=g_pos, g_q=g_q, g_iso=float(-Fbar.sum()), g_t=float(np.sum(g_e * db)), u=u, rho=rho,
+                iters=iters, relres=relres, status=st, g_e=g_e)
 
 
 def isotropic_C(E=1.0, nu=0.3) -> np.ndarray:

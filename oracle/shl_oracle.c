@@ -10,7 +10,8 @@
  * Everything is IEEE double, built without fast-math and without FMA
  * contraction.  OpenMP only splits independent outputs (points, rows,
  * elements) across threads; every reduction is summed in a fixed order, so
- * results do not depend on the thread count.
+ * results do not depend on the thread count (except shlo_field_vjp, whose
+ * per-thread partial sums make its last bits depend on it).
  *
  * Conventions (shared with the CUDA library by definition, not by code):
  *   - unit cell [0,1)^3, r voxels per axis, h = 1/r;
@@ -628,4 +629,99 @@ int shlo_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/*
+ * Vector-Jacobian product of the field (chain rule of Eq. chain through F and
+ * grad F): given per-point seeds Fbar = dE/dF(p) and gFbar = dE/d(grad F)(p),
+ *   g_q[j]   += sum_p Fbar dF/dq_j + gFbar . d(grad F)/dq_j
+ *   g_pos[j] += sum_p Fbar dF/dx_j + gFbar . d(grad F)/dx_j
+ * where, for B_j(p) = sum_hkl alpha w / |n|^2 cos cos cos (charge j's basis
+ * sum), F = sum_j q_j B_j, dF/dq_j = B_j, d(grad F)/dq_j = grad B_j,
+ * dF/dx_j = -q_j grad B_j and d(grad F)_a/dx_jm = -q_j d_a d_m B_j (every
+ * factor depends on p - p_j).  Points are split across threads; per-thread
+ * partial sums are added in thread order.
+ */
+int shlo_field_vjp(int nc, const double *pos, const double *q, const double *alpha, int K, long npts,
+                   const double *pts, const double *Fbar, const double *gFbar, double *g_pos, double *g_q) {
+    if (nc < 0 || K < 1 || K > 15 || npts < 0) return 1;
+    const int K1 = K + 1;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    double *acc = (double *)calloc((size_t)nthr * nc * 4, sizeof(double));
+    if (!acc) return 2;
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *my = acc + (size_t)tid * nc * 4;
+        double cs[3][16], sn[3][16];
+#pragma omp for schedule(static)
+        for (long p = 0; p < npts; ++p) {
+            for (int j = 0; j < nc; ++j) {
+                for (int d = 0; d < 3; ++d)
+                    for (int n = 0; n <= K; ++n) {
+                        const double a = 2.0 * SHLO_PI * n * (pts[3 * p + d] - pos[3 * j + d]);
+                        cs[d][n] = cos(a);
+                        sn[d][n] = sin(a);
+                    }
+                double B = 0.0, g[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                for (int h = 0; h <= K; ++h)
+                    for (int k = 0; k <= K; ++k)
+                        for (int l = 0; l <= K; ++l) {
+                            if (h == 0 && k == 0 && l == 0) continue;
+                            const double a = alpha ? alpha[(h * K1 + k) * K1 + l] : 1.0;
+                            const double coef = a * shlo_weight(h, k, l) / (double)(h * h + k * k + l * l);
+                            const double w[3] = {2.0 * SHLO_PI * h, 2.0 * SHLO_PI * k, 2.0 * SHLO_PI * l};
+                            const int nn[3] = {h, k, l};
+                            double c[3], s[3];
+                            for (int d = 0; d < 3; ++d) {
+                                c[d] = cs[d][nn[d]];
+                                s[d] = sn[d][nn[d]];
+                            }
+                            B += coef * c[0] * c[1] * c[2];
+                            for (int d = 0; d < 3; ++d) {
+                                double t = -w[d] * s[d];
+                                for (int e = 0; e < 3; ++e)
+                                    if (e != d) t *= c[e];
+                                g[d] += coef * t;
+                            }
+                            for (int d = 0; d < 3; ++d)
+                                for (int m = 0; m < 3; ++m) {
+                                    double t;
+                                    if (d == m) {
+                                        t = -w[d] * w[d] * c[0] * c[1] * c[2];
+                                    } else {
+                                        const int o = 3 - d - m;
+                                        t = w[d] * s[d] * w[m] * s[m] * c[o];
+                                    }
+                                    H[d][m] += coef * t;
+                                }
+                        }
+                const double fb = Fbar[p];
+                const double *gb = gFbar + 3 * p;
+                my[4 * j + 0] += fb * B + gb[0] * g[0] + gb[1] * g[1] + gb[2] * g[2];
+                for (int m = 0; m < 3; ++m) {
+                    double t = fb * g[m];
+                    for (int a2 = 0; a2 < 3; ++a2) t += gb[a2] * H[a2][m];
+                    my[4 * j + 1 + m] += -q[j] * t;
+                }
+            }
+        }
+    }
+    for (int j = 0; j < nc; ++j) {
+        g_q[j] = 0.0;
+        g_pos[3 * j] = g_pos[3 * j + 1] = g_pos[3 * j + 2] = 0.0;
+        for (int t = 0; t < nthr; ++t) {
+            const double *my = acc + (size_t)t * nc * 4;
+            g_q[j] += my[4 * j];
+            for (int m = 0; m < 3; ++m) g_pos[3 * j + m] += my[4 * j + 1 + m];
+        }
+    }
+    free(acc);
+    return 0;
 }
