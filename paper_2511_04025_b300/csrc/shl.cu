@@ -5,6 +5,7 @@
 #include "element.cuh"
 #include "field.cuh"
 #include "pcg.cuh"
+#include "adjoint.cuh"
 
 #include <atomic>
 
@@ -634,6 +635,103 @@ inline size_t design_footprint(int r, const shl_solve_opts *o) {
     return N * per + ((size_t)8 << 20);
 }
 
+// Gradient of an objective E(C^H) with dE/dC^H = dEdC (host, 36) w.r.t.
+// charge positions/magnitudes, iso-level, half-thickness and alpha (Eq. chain),
+// through the smoothed density.  Arguments validated, lock held.
+inline int grad_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_opts *o, const double *dEdC,
+                     double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t,
+                     double *g_alpha, shl_stats *st, cudaStream_t s) {
+    const size_t N = (size_t)r * r * r;
+    const int nb = 2 * d->K + 1;
+    double *F = nullptr, *gF = nullptr, *dd = nullptr, *rho = nullptr, *g = nullptr, *QR = nullptr, *Abar = nullptr,
+           *Gd = nullptr, *gout = nullptr, *partial = nullptr;
+    unsigned *ticket = nullptr;
+    SHL_TRY(ws_get_t(ctx, "adj_F", N, &F));
+    SHL_TRY(ws_get_t(ctx, "adj_gF", 3 * N, &gF));
+    SHL_TRY(ws_get_t(ctx, "adj_d", N, &dd));
+    SHL_TRY(ws_get_t(ctx, "adj_rho", N, &rho));
+    SHL_TRY(ws_get_t(ctx, "adj_g", N, &g));
+    SHL_TRY(ws_get_t(ctx, "adj_QR", (size_t)r * 2 * nb * nb, &QR));
+    SHL_TRY(ws_get_t(ctx, "adj_Abar", (size_t)nb * nb * nb, &Abar));
+    SHL_TRY(ws_get_t(ctx, "adj_small", 64, &Gd));
+    gout = Gd + 40;
+    if (st) std::memset(st, 0, sizeof(*st));
+    // forward: distances, t (held fixed), smoothed density, F and grad F
+    VoxOut v;
+    SHL_TRY(run_voxelize(ctx, d, r, o->kappa, nullptr, rho, dd, s, &v));
+    const double kappa = o->kappa > 0.0 ? o->kappa : std::log(9.0) * r;
+    SHL_TRY(run_field(ctx, d, r, F, gF, nullptr, s));
+    // six cell problems and C^H
+    const size_t NV = 18 * N;
+    double *x64 = u_dev;
+    if (!x64) SHL_TRY(ws_get_t(ctx, "adj_x64", NV, &x64));
+    int rc = solve_impl(ctx, r, nullptr, rho, o, x64, o->warm_start && u_dev, C_out, st, s);
+    if (st) {
+        st->t = v.t;
+        st->margin = v.margin;
+        st->n_solid = v.n_solid;
+        st->n_ambiguous = v.n_amb;
+    }
+    if (rc != SHL_OK && rc != SHL_ENOCONV) return rc;
+    // element sensitivities g_e = dE/drho_e
+    SHL_CUDA(ctx, cudaMemcpyAsync(Gd, dEdC, 36 * sizeof(double), cudaMemcpyHostToDevice, s));
+    {
+        ElemOp<double> op;
+        SHL_TRY(get_op(ctx, o->nu, r, &op));
+        ChomArgs a{};
+        a.r = r;
+        a.N = N;
+        a.u = x64;
+        a.rho = rho;
+        a.E = o->E;
+        a.Evoid = o->E_void;
+        a.G = Gd;
+        a.g = g;
+        a.op = op;
+        const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
+        cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        chom_kernel<<<grid1d(N, kChomThreads, 148 * 8), kChomThreads, smem, s>>>(a);
+        ++ctx->launches;
+    }
+    // seeds for F, grad F; dE/dt, dE/dc
+    const int gs = grid1d(N, kBlk, 148 * 4);
+    SHL_TRY(ws_get_t(ctx, "adj_partial", (size_t)gs * 2, &partial));
+    SHL_TRY(ws_get_t(ctx, "adj_ticket", 1, &ticket));
+    SeedArgs sa{N, F, gF, rho, g, d->iso, kappa, partial, ticket, gout};
+    adj_seed_kernel<<<gs, kBlk, 0, s>>>(sa);
+    ++ctx->launches;
+    // back through the separable field to the coefficient tensor and the charges
+    const size_t smp = sizeof(double) * ((size_t)r * nb + (size_t)r * 3 * nb);
+    cudaFuncSetAttribute(adj_plane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+    adj_plane_kernel<<<r, 256, smp, s>>>(r, d->K, F, gF, QR);
+    const size_t smc = sizeof(double) * (size_t)r * nb;
+    cudaFuncSetAttribute(adj_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    adj_coef_kernel<<<1, 512, smc, s>>>(r, d->K, QR, Abar);
+    Uploaded up;
+    SHL_TRY(upload_design(ctx, d, s, &up, "grad"));
+    double *gp = nullptr;
+    const int na = (d->K + 1) * (d->K + 1) * (d->K + 1);
+    SHL_TRY(ws_get_t(ctx, "adj_gcharges", (size_t)4 * d->n + na, &gp));
+    adj_charge_kernel<<<(d->n + 127) / 128, 128, 0, s>>>(d->n, d->K, up.pos, up.q, up.alpha, Abar, gp, gp + 3 * d->n);
+    ctx->launches += 3;
+    if (g_alpha) {
+        adj_alpha_kernel<<<1, 256, 0, s>>>(d->n, d->K, up.pos, up.q, Abar, gp + 4 * d->n);
+        ++ctx->launches;
+    }
+    SHL_CUDA(ctx, cudaGetLastError());
+    std::vector<double> hg((size_t)4 * d->n + na);
+    double ho[2];
+    SHL_CUDA(ctx, cudaMemcpyAsync(hg.data(), gp, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaMemcpyAsync(ho, gout, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    if (g_pos) std::memcpy(g_pos, hg.data(), sizeof(double) * 3 * d->n);
+    if (g_q) std::memcpy(g_q, hg.data() + 3 * d->n, sizeof(double) * d->n);
+    if (g_alpha) std::memcpy(g_alpha, hg.data() + 4 * d->n, sizeof(double) * na);
+    if (g_t) *g_t = ho[0];
+    if (g_iso) *g_iso = ho[1];
+    return rc;
+}
+
 }  // namespace shl
 
 #include "serve.cuh"
@@ -822,6 +920,22 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
     if (!C_out) return set_err(ctx, SHL_EINVAL, "C_out is NULL");
     cudaSetDevice(ctx->device);
     return homogenize_impl(ctx, d, r, o, C_out, st, pick_stream(ctx, stream), nullptr, false);
+}
+
+int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, const double *dE_dC,
+             double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t, double *g_alpha,
+             shl_stats *st, void *stream) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    SHL_TRY(validate_solve_opts(ctx, o));
+    SHL_TRY(validate_design(ctx, d, r));
+    if (o->density != SHL_SMOOTH)
+        return set_err(ctx, SHL_EINVAL, "shl_grad needs the smooth density (the binary mask has no derivative)");
+    if (!dE_dC) return set_err(ctx, SHL_EINVAL, "dE_dC is NULL");
+    for (int i = 0; i < 36; ++i)
+        if (!std::isfinite(dE_dC[i])) return set_err(ctx, SHL_EINVAL, "non-finite dE_dC");
+    cudaSetDevice(ctx->device);
+    return grad_impl(ctx, d, r, o, dE_dC, u_dev, C_out, g_pos, g_q, g_iso, g_t, g_alpha, st, pick_stream(ctx, stream));
 }
 
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
