@@ -58,6 +58,7 @@ typedef enum {
 
 typedef enum { SHL_FP64 = 0, SHL_FP32_REFINE = 1 } shl_precision;
 typedef enum { SHL_MASK = 0, SHL_SMOOTH = 1 } shl_density;
+typedef enum { SHL_PRECOND_JACOBI = 0, SHL_PRECOND_MG = 1 } shl_precond;
 
 typedef struct shl_ctx shl_ctx;
 
@@ -117,6 +118,14 @@ typedef struct {
  *                  (<= 0 selects 1e-2)
  *   warm_start     use the displacements passed in (shl_solve) or kept for the
  *                  session (serving) as the initial guess
+ *   precond        SHL_PRECOND_MG (default): geometric multigrid V-cycle
+ *                  (Sec. 4.2: 2x2x2 coarsening, Galerkin coarse operators,
+ *                  damped block-Jacobi smoothing, pinned dense solve on the
+ *                  coarsest level) in FP32, used in SHL_FP32_REFINE mode when r
+ *                  halves down to a coarsest grid of at most 6^3 nodes;
+ *                  otherwise, and in SHL_FP64 mode, point Jacobi.
+ *   mg_nu          smoothing sweeps before and after the coarse correction (<= 0: 2)
+ *   mg_omega       block-Jacobi damping (<= 0: 0.6)
  */
 typedef struct {
     double E, nu, E_void;
@@ -127,6 +136,9 @@ typedef struct {
     int32_t warm_start;
     double kappa;
     double inner_tol;
+    int32_t precond;
+    int32_t mg_nu;
+    double mg_omega;
 } shl_solve_opts;
 
 /* Per-result record. */

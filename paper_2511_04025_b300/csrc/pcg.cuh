@@ -13,9 +13,10 @@ struct VecArgs {
     size_t N;
     T *x, *r, *p;
     const T *q;
-    const T *dinv;
+    const T *dinv;  // point-Jacobi inverse diagonal (Jacobi mode)
     PcgState *st;
     double *partial;
+    const T *z;     // preconditioned residual M^-1 r (multigrid mode; null for Jacobi)
 };
 
 // x += alpha p ; r -= alpha q ; z = D^-1 r ; partial (r.z, r.r)
@@ -34,7 +35,7 @@ __global__ void pcg_update_kernel(VecArgs<T> a) {
     DotAcc<T> dacc[12];
     const size_t N = a.N;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const T di = a.dinv[n];
+        const T di = a.z ? T(0) : a.dinv[n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             if (!act[k]) continue;
@@ -45,7 +46,7 @@ __global__ void pcg_update_kernel(VecArgs<T> a) {
                 a.x[o] += al[k] * pv;
                 const T rv = a.r[o] - al[k] * qv;
                 a.r[o] = rv;
-                dacc[k].add(rv * (di * rv));
+                if (!a.z) dacc[k].add(rv * (di * rv));
                 dacc[6 + k].add(rv * rv);
             }
         }
@@ -72,7 +73,7 @@ __global__ void pcg_update_kernel(VecArgs<T> a) {
                 st->active[k] = 0;
             } else if (st->iters[k] >= st->maxit) {
                 st->active[k] = 0;
-            } else {
+            } else if (!a.z) {
                 st->beta[k] = rz / st->rz[k];
                 st->rz[k] = rz;
             }
@@ -80,6 +81,83 @@ __global__ void pcg_update_kernel(VecArgs<T> a) {
         for (int k = 0; k < 6; ++k) na += st->active[k];
         st->nactive = na;
     }
+}
+
+// Multigrid mode: rz = r . z after the V-cycle; beta = rz_new / rz_old.
+template <typename T>
+__global__ void pcg_rz_kernel(VecArgs<T> a) {
+    PcgState *st = a.st;
+    if (st->nactive == 0) return;
+    bool act[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) act[k] = st->active[k] != 0;
+    DotAcc<T> dacc[6];
+    const size_t N = a.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!act[k]) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                dacc[k].add(a.r[o] * a.z[o]);
+            }
+        }
+    }
+    double acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = dacc[k].get();
+    block_reduce_store<6>(acc, a.partial, blockIdx.x);
+    if (!last_block_ticket(&st->ticket_aux, gridDim.x)) return;
+    __shared__ double tot[6];
+    sum_partials_ordered<6>(a.partial, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) {
+            if (!act[k]) continue;
+            if (!isfinite(tot[k]) || !(tot[k] > 0.0)) {
+                st->numeric_err = 1;
+                st->active[k] = 0;
+                continue;
+            }
+            st->beta[k] = tot[k] / st->rz[k];
+            st->rz[k] = tot[k];
+        }
+        int na = 0;
+        for (int k = 0; k < 6; ++k) na += st->active[k];
+        st->nactive = na;
+    }
+}
+
+// Multigrid mode, (re)start of the direction for the load cases in mask:
+// p = z, rz = r . z.
+template <typename T>
+__global__ void pcg_restart_z_kernel(VecArgs<T> a, int mask) {
+    PcgState *st = a.st;
+    DotAcc<T> dacc[6];
+    const size_t N = a.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!((mask >> k) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * N + n;
+                const T zv = a.z[o];
+                a.p[o] = zv;
+                dacc[k].add(a.r[o] * zv);
+            }
+        }
+    }
+    double acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = dacc[k].get();
+    block_reduce_store<6>(acc, a.partial, blockIdx.x);
+    if (!last_block_ticket(&st->ticket_aux, gridDim.x)) return;
+    __shared__ double tot[6];
+    sum_partials_ordered<6>(a.partial, gridDim.x, tot);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k)
+            if ((mask >> k) & 1) st->rz[k] = tot[k];
 }
 
 // p = D^-1 r + beta p
@@ -96,14 +174,14 @@ __global__ void pcg_direction_kernel(VecArgs<T> a) {
     }
     const size_t N = a.N;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const T di = a.dinv[n];
+        const T di = a.z ? T(0) : a.dinv[n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             if (!act[k]) continue;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
-                a.p[o] = di * a.r[o] + be[k] * a.p[o];
+                a.p[o] = (a.z ? a.z[o] : di * a.r[o]) + be[k] * a.p[o];
             }
         }
     }
@@ -117,7 +195,7 @@ __global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
     DotAcc<T> dacc[12];
     const size_t N = a.N;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const T di = a.dinv[n];
+        const T di = a.z ? T(0) : a.dinv[n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             if (!((want_mask >> k) & 1)) continue;
@@ -125,7 +203,7 @@ __global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
                 const T rv = a.r[o];
-                const T z = di * rv;
+                const T z = a.z ? a.z[o] : di * rv;
                 a.p[o] = z;
                 dacc[k].add(rv * z);
                 dacc[6 + k].add(rv * rv);
@@ -195,7 +273,7 @@ __global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, int 
     DotAcc<float> dacc[12];
     const size_t N = a.N;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const float di = a.dinv[n];
+        const float di = a.z ? 0.0f : a.dinv[n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             if (!((mask >> k) & 1)) continue;
@@ -203,10 +281,12 @@ __global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, int 
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
                 const float rn = (float)r64[o];
-                if ((restart >> k) & 1)
-                    a.p[o] = di * rn;
-                else
-                    a.p[o] += di * (rn - a.r[o]);
+                if (!a.z) {
+                    if ((restart >> k) & 1)
+                        a.p[o] = di * rn;
+                    else
+                        a.p[o] += di * (rn - a.r[o]);
+                }
                 a.r[o] = rn;
                 dacc[k].add(rn * (di * rn));
                 dacc[6 + k].add(rn * rn);

@@ -6,6 +6,7 @@
 #include "field.cuh"
 #include "pcg.cuh"
 #include "adjoint.cuh"
+#include "mg.cuh"
 
 #include <atomic>
 
@@ -307,6 +308,7 @@ struct SolveOut {
     double relres[6] = {0, 0, 0, 0, 0, 0};
     int n_refine = 0;
     int status = SHL_OK;
+    int precond = SHL_PRECOND_JACOBI;
 };
 
 // Residual f - K x (FP64) with its squared norms per load case; pin selects
@@ -335,6 +337,216 @@ inline int host_pinned(shl_ctx *ctx, HostPinned *hp) {
         SHL_CUDA(ctx, cudaMallocHost(&cache.v, sizeof(double) * 64));
     }
     *hp = cache;
+    return SHL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid preconditioner (mg.cuh): plan, per-density setup, V-cycle
+// ---------------------------------------------------------------------------
+struct MgLevel {
+    int r = 0;
+    size_t N = 0;
+    float *S = nullptr;     // stencil (levels >= 1)
+    float *Dinv = nullptr;  // 3x3 block-Jacobi inverses
+    float *x = nullptr, *b = nullptr, *t = nullptr;
+};
+
+struct Mg {
+    int L = 0;  // coarsest level index
+    MgLevel lv[kMgMaxLevels];
+    float *Ainv = nullptr;  // coarsest dense inverse
+    int n3 = 0;
+    float omega = 0.6f;
+    int nu = 2;
+};
+
+// Levels: halve while even and >= 6; usable when the coarsest is small.
+inline bool mg_plan(int r, Mg *mg) {
+    int rl = r, L = 0;
+    while (rl % 2 == 0 && rl >= 6 && L + 1 < kMgMaxLevels) {
+        rl /= 2;
+        ++L;
+    }
+    if (L == 0 || (size_t)rl * rl * rl > (size_t)kMgMaxCoarse) return false;
+    mg->L = L;
+    for (int l = 0, rr = r; l <= L; ++l, rr /= 2) {
+        mg->lv[l].r = rr;
+        mg->lv[l].N = (size_t)rr * rr * rr;
+    }
+    return true;
+}
+
+inline int mg_constants(shl_ctx *ctx, double nu) {
+    static std::mutex mu;
+    static std::map<std::pair<int, double>, bool> done;  // (device, nu) uploaded
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, nu})) return SHL_OK;
+    static float Mc[8][24][24];
+    const double err = build_child_matrices(nu, Mc);
+    if (!(err < 1e-12)) return set_err(ctx, SHL_EINVAL, "child matrices do not sum to the coarse element (%g)", err);
+    done.clear();  // the constant bank holds one Poisson ratio per device at a time
+    SHL_CUDA(ctx, cudaMemcpyToSymbol(c_child_M, Mc, sizeof(Mc)));
+    done[{dev, nu}] = true;
+    return SHL_OK;
+}
+
+inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opts *o, Mg *mg, cudaStream_t s) {
+    SHL_TRY(mg_constants(ctx, o->nu));
+    mg->omega = (float)(o->mg_omega > 0.0 ? o->mg_omega : 0.6);
+    mg->nu = o->mg_nu > 0 ? o->mg_nu : 2;
+    char nm[64];
+    for (int l = 0; l <= mg->L; ++l) {
+        MgLevel &L = mg->lv[l];
+        snprintf(nm, sizeof(nm), "mg_dinv%d", l);
+        SHL_TRY(ws_get_t(ctx, nm, L.N * 9, &L.Dinv));
+        snprintf(nm, sizeof(nm), "mg_t%d", l);
+        SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.t));
+        if (l >= 1) {
+            snprintf(nm, sizeof(nm), "mg_S%d", l);
+            SHL_TRY(ws_get_t(ctx, nm, L.N * 27 * 9, &L.S));
+            snprintf(nm, sizeof(nm), "mg_x%d", l);
+            SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.x));
+            snprintf(nm, sizeof(nm), "mg_b%d", l);
+            SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.b));
+        }
+    }
+    // fine block-Jacobi
+    double Ku[24][24];
+    unit_hex8_stiffness(o->nu, Ku);
+    CornerBlocks cb;
+    for (int b = 0; b < 8; ++b)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) cb.K[b][3 * i + j] = (float)(Ku[3 * b + i][3 * b + j] / r);
+    mg_dinv_fine_kernel<<<grid1d(mg->lv[0].N), kBlk, 0, s>>>(r, den.mask, den.rho, (float)den.E, (float)den.Ev, cb,
+                                                             mg->lv[0].Dinv);
+    ++ctx->launches;
+    for (int l = 1; l <= mg->L; ++l) {
+        MgLevel &L = mg->lv[l];
+        const int g = grid1d(L.N * 27, kBlk, 148 * 16);
+        if (l == 1)
+            mg_galerkin_fine_kernel<<<g, kBlk, 0, s>>>(L.r, den.mask, den.rho, (float)den.E, (float)den.Ev,
+                                                       (float)(1.0 / r), L.S);
+        else
+            mg_galerkin_coarse_kernel<<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S);
+        mg_dinv_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.N, L.S, L.Dinv);
+        ctx->launches += 2;
+    }
+    SHL_CUDA(ctx, cudaGetLastError());
+    // coarsest: dense, coarse node 0 pinned, inverted in FP64 on the host
+    const MgLevel &C = mg->lv[mg->L];
+    const int n3 = (int)(3 * C.N);
+    mg->n3 = n3;
+    std::vector<float> Sh(C.N * 243);
+    SHL_CUDA(ctx, cudaMemcpyAsync(Sh.data(), C.S, Sh.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    const int m = n3 - 3;  // pinned: DOFs of node 0 removed
+    std::vector<double> A((size_t)m * m, 0.0);
+    const int rc = C.r;
+    for (size_t I = 0; I < C.N; ++I) {
+        const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
+        for (int dl = 0; dl < 27; ++dl) {
+            const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+            const size_t J = ((size_t)wrapi(iz + dz, rc) * rc + wrapi(iy + dy, rc)) * rc + wrapi(ix + dx, rc);
+            if (I == 0 || J == 0) continue;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    A[(3 * (I - 1) + i) * (size_t)m + 3 * (J - 1) + j] += Sh[(I * 27 + dl) * 9 + 3 * i + j];
+        }
+    }
+    // symmetrise (FP32 stencil rounding), Cholesky, explicit inverse
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < i; ++j) A[(size_t)i * m + j] = A[(size_t)j * m + i] = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
+    std::vector<double> Lc((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        double d = A[(size_t)j * m + j];
+        for (int k = 0; k < j; ++k) d -= Lc[(size_t)j * m + k] * Lc[(size_t)j * m + k];
+        if (!(d > 0.0)) return set_err(ctx, SHL_ENUMERIC, "coarsest multigrid operator is not positive definite");
+        const double ljj = std::sqrt(d);
+        Lc[(size_t)j * m + j] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            double v = A[(size_t)i * m + j];
+            for (int k = 0; k < j; ++k) v -= Lc[(size_t)i * m + k] * Lc[(size_t)j * m + k];
+            Lc[(size_t)i * m + j] = v / ljj;
+        }
+    }
+    std::vector<float> Ainv((size_t)n3 * n3, 0.0f);
+    std::vector<double> col(m);
+    for (int c = 0; c < m; ++c) {
+        for (int i = 0; i < m; ++i) col[i] = (i == c) ? 1.0 : 0.0;
+        for (int i = 0; i < m; ++i) {  // L y = e_c
+            double v = col[i];
+            for (int k = 0; k < i; ++k) v -= Lc[(size_t)i * m + k] * col[k];
+            col[i] = v / Lc[(size_t)i * m + i];
+        }
+        for (int i = m - 1; i >= 0; --i) {  // L^T x = y
+            double v = col[i];
+            for (int k = i + 1; k < m; ++k) v -= Lc[(size_t)k * m + i] * col[k];
+            col[i] = v / Lc[(size_t)i * m + i];
+        }
+        for (int i = 0; i < m; ++i) Ainv[(size_t)(i + 3) * n3 + (c + 3)] = (float)col[i];
+    }
+    SHL_TRY(ws_get_t(ctx, "mg_Ainv", (size_t)n3 * n3, &mg->Ainv));
+    SHL_CUDA(ctx, cudaMemcpyAsync(mg->Ainv, Ainv.data(), Ainv.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    return SHL_OK;
+}
+
+// z = V-cycle(b) for the pinned fine system; `fine` carries the density and
+// operator of the matrix-free apply.
+inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const float *b0, float *x0, PcgState *st,
+                     cudaStream_t s) {
+    const float w = mg->omega;
+    auto apply_level = [&](int l, const float *x, float *t) -> int {
+        if (l == 0) {
+            ApplyArgs<float> a = fine;
+            a.p = x;
+            a.q = t;
+            a.pin = 1;
+            a.dot = 0;
+            a.resid = 0;
+            a.st = st;
+            return launch_apply<float>(ctx, a, s);
+        }
+        const MgLevel &L = mg->lv[l];
+        mg_stencil_apply_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, x, t, st);
+        ++ctx->launches;
+        return SHL_OK;
+    };
+    mg->lv[0].b = const_cast<float *>(b0);
+    mg->lv[0].x = x0;
+    for (int l = 0; l < mg->L; ++l) {  // down: pre-smooth, restrict the residual
+        MgLevel &L = mg->lv[l];
+        const int g = grid1d(L.N);
+        mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, w, L.x, 1, st);
+        ++ctx->launches;
+        for (int it = 1; it < mg->nu; ++it) {
+            SHL_TRY(apply_level(l, L.x, L.t));
+            mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, w, L.x, 0, st);
+            ++ctx->launches;
+        }
+        SHL_TRY(apply_level(l, L.x, L.t));
+        mg_restrict_kernel<<<grid1d(mg->lv[l + 1].N), kBlk, 0, s>>>(mg->lv[l + 1].r, L.b, L.t, mg->lv[l + 1].b, st);
+        ++ctx->launches;
+    }
+    {
+        MgLevel &C = mg->lv[mg->L];
+        mg_dense_solve_kernel<<<grid1d((size_t)6 * mg->n3, 128), 128, 0, s>>>(mg->n3, mg->Ainv, C.b, C.x, st);
+        ++ctx->launches;
+    }
+    for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
+        MgLevel &L = mg->lv[l];
+        const int g = grid1d(L.N);
+        mg_prolong_kernel<<<g, kBlk, 0, s>>>(mg->lv[l + 1].r, mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
+        ++ctx->launches;
+        for (int it = 0; it < mg->nu; ++it) {
+            SHL_TRY(apply_level(l, L.x, L.t));
+            mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, w, L.x, 0, st);
+            ++ctx->launches;
+        }
+    }
+    SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
 }
 
@@ -434,17 +646,27 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             const size_t gv = grid1d(N, kBlk, 148 * 4);
             double *partial = nullptr;
             SHL_TRY(ws_get_t(ctx, "pcg_partial", (size_t)gv * 12, &partial));
-            VecArgs<float> va{N, b.x, b.r, b.p, b.q, b.dinv, st, partial};
+            // multigrid preconditioner (when the grid coarsens far enough)
+            Mg mg;
+            const bool use_mg = (o->precond == SHL_PRECOND_MG) && mg_plan(r, &mg);
+            float *z32 = nullptr;
+            if (use_mg) {
+                SHL_TRY(ws_get_t(ctx, "z32", NV, &z32));
+                SHL_TRY(mg_setup(ctx, r, den, o, &mg, s));
+            }
+            out->precond = use_mg ? SHL_PRECOND_MG : SHL_PRECOND_JACOBI;
+            VecArgs<float> va{N, b.x, b.r, b.p, b.q, b.dinv, st, partial, z32};
+            ApplyArgs<float> a = make_apply<float>(r, den, op32);
+            if (use_mg) SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, nullptr, s));
             pcg_init_kernel<float><<<gv, kBlk, 0, s>>>(va, want, 0);
             ++ctx->launches;
-            ApplyArgs<float> a = make_apply<float>(r, den, op32);
             a.p = b.p;
             a.q = b.q;
             a.pin = 1;
             a.dot = 1;
             a.st = st;
             a.ticket = &st->ticket_apply;
-            const int chunk = 32;
+            const int chunk = use_mg ? 4 : 32;
             PcgState hst;
             for (long long it = 0;; it += chunk) {
                 if (it > (long long)maxit + 2 * chunk)
@@ -452,8 +674,14 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                 for (int c = 0; c < chunk; ++c) {
                     SHL_TRY(launch_apply<float>(ctx, a, s));
                     pcg_update_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                    ++ctx->launches;
+                    if (use_mg) {
+                        SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s));
+                        pcg_rz_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                        ++ctx->launches;
+                    }
                     pcg_direction_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                    ctx->launches += 2;
+                    ++ctx->launches;
                 }
                 SHL_CUDA(ctx, cudaGetLastError());
                 SHL_CUDA(ctx, cudaMemcpyAsync(&hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
@@ -477,6 +705,11 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                     SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
                     reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, r64, mask, restart, rr_true);
                     ++ctx->launches;
+                    if (use_mg) {  // direction restarts from the preconditioned true residual
+                        SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, nullptr, s));
+                        pcg_restart_z_kernel<float><<<gv, kBlk, 0, s>>>(va, mask);
+                        ++ctx->launches;
+                    }
                     SHL_CUDA(ctx, cudaMemcpyAsync(&hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
                     SHL_CUDA(ctx, cudaMemcpyAsync(hp.v, norms + 12, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
                     SHL_CUDA(ctx, cudaStreamSynchronize(s));
@@ -550,6 +783,9 @@ inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
         return set_err(ctx, SHL_EINVAL, "unknown precision %d", o->precision);
     if (o->density != SHL_MASK && o->density != SHL_SMOOTH)
         return set_err(ctx, SHL_EINVAL, "unknown density mode %d", o->density);
+    if (o->precond != SHL_PRECOND_JACOBI && o->precond != SHL_PRECOND_MG)
+        return set_err(ctx, SHL_EINVAL, "unknown preconditioner %d", o->precond);
+    if (!(o->mg_omega <= 0.0 || o->mg_omega < 2.0)) return set_err(ctx, SHL_EINVAL, "mg_omega must be < 2");
     return SHL_OK;
 }
 
@@ -767,6 +1003,9 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->density = SHL_MASK;
     o->kappa = 0.0;
     o->inner_tol = 1e-2;
+    o->precond = SHL_PRECOND_MG;
+    o->mg_nu = 2;
+    o->mg_omega = 0.6;
 }
 
 int shl_create(const shl_opts *opts, shl_ctx **out) {

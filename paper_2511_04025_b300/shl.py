@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libshl.so")
 SHL_OK, SHL_EINVAL, SHL_ENOMEM, SHL_ENOCONV, SHL_ENUMERIC, SHL_ECUDA, SHL_EAGAIN, SHL_ENOTFOUND = range(8)
 SHL_FP64, SHL_FP32_REFINE = 0, 1
 SHL_MASK, SHL_SMOOTH = 0, 1
+SHL_PRECOND_JACOBI, SHL_PRECOND_MG = 0, 1
 STATUS_NAMES = ["SHL_OK", "SHL_EINVAL", "SHL_ENOMEM", "SHL_ENOCONV", "SHL_ENUMERIC", "SHL_ECUDA", "SHL_EAGAIN",
                 "SHL_ENOTFOUND"]
 
@@ -41,7 +42,8 @@ class shl_solve_opts(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("E_void", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("density", ctypes.c_int32), ("warm_start", ctypes.c_int32), ("kappa", ctypes.c_double),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int32), ("mg_nu", ctypes.c_int32),
+                ("mg_omega", ctypes.c_double)]
 
 
 class shl_stats(ctypes.Structure):
