@@ -115,7 +115,7 @@ typedef struct {
  *   density        SHL_MASK: binary rho; SHL_SMOOTH: rho = 1/(1+exp(-kappa(t-d)))
  *   kappa          logistic sharpness; <= 0 selects ln(9) * r (two-voxel rise)
  *   inner_tol      FP32_REFINE: residual reduction between reliable updates
- *                  (<= 0 selects 1e-2)
+ *                  (<= 0 selects 1e-3)
  *   warm_start     use the displacements passed in (shl_solve) or kept for the
  *                  session (serving) as the initial guess
  *   precond        SHL_PRECOND_MG (default): geometric multigrid V-cycle
@@ -124,8 +124,11 @@ typedef struct {
  *                  coarsest level) in FP32, used in SHL_FP32_REFINE mode when r
  *                  halves down to a coarsest grid of at most 6^3 nodes;
  *                  otherwise, and in SHL_FP64 mode, point Jacobi.
- *   mg_nu          smoothing sweeps before and after the coarse correction (<= 0: 2)
- *   mg_omega       block-Jacobi damping (<= 0: 0.6)
+ *   mg_nu          smoothing sweeps before and after the coarse correction (<= 0: 1)
+ *   mg_omega       block-Jacobi damping as omega * lambda_max(D^-1 A) per level,
+ *                  lambda_max estimated by power iteration at setup (<= 0: 1.4);
+ *                  if the preconditioned CG still breaks down, the solve is
+ *                  repeated with point Jacobi
  */
 typedef struct {
     double E, nu, E_void;

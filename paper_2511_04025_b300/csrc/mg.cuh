@@ -106,7 +106,7 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
             }
         }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) S[(I * 27 + dl) * 9 + m] = h * acc[m];
+        for (int m = 0; m < 9; ++m) S[(size_t)(dl * 9 + m) * Nc + I] = h * acc[m];
     }
 }
 
@@ -114,6 +114,7 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
 __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc) {
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
+    const size_t Nf = (size_t)rf * rf * rf;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27; t += (size_t)gridDim.x * blockDim.x) {
         const size_t I = t / 27;
         const int dl = (int)(t % 27);
@@ -132,13 +133,13 @@ __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, 
                                 const float wb = tri_w(ax + bx - 2 * dx, ay + by - 2 * dy, az + bz - 2 * dz);
                                 if (wb == 0.0f) continue;
                                 const float w = wa * wb;
-                                const float *blk = Sf + (fi * 27 + (bz + 1) * 9 + (by + 1) * 3 + (bx + 1)) * 9;
+                                const int bl = (bz + 1) * 9 + (by + 1) * 3 + (bx + 1);
 #pragma unroll
-                                for (int m = 0; m < 9; ++m) acc[m] += w * blk[m];
+                                for (int m = 0; m < 9; ++m) acc[m] += w * Sf[(size_t)(bl * 9 + m) * Nf + fi];
                             }
                 }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) Sc[(I * 27 + dl) * 9 + m] = acc[m];
+        for (int m = 0; m < 9; ++m) Sc[(size_t)(dl * 9 + m) * Nc + I] = acc[m];
     }
 }
 
@@ -161,9 +162,9 @@ __device__ inline void inv3(const double a[9], double o[9]) {
 __global__ void mg_dinv_stencil_kernel(size_t N, const float *S, float *Dinv) {
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         double a[9], o[9];
-        for (int m = 0; m < 9; ++m) a[m] = S[(n * 27 + 13) * 9 + m];
+        for (int m = 0; m < 9; ++m) a[m] = S[(size_t)(13 * 9 + m) * N + n];
         inv3(a, o);
-        for (int m = 0; m < 9; ++m) Dinv[n * 9 + m] = (float)o[m];
+        for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = (float)o[m];
     }
 }
 
@@ -186,7 +187,7 @@ __global__ void mg_dinv_fine_kernel(int r, const uint8_t *mask, const double *rh
             for (int m = 0; m < 9; ++m) a[m] += Ee * cb.K[b][m];
         }
         inv3(a, o);
-        for (int m = 0; m < 9; ++m) Dinv[n * 9 + m] = n == 0 ? 0.0f : (float)o[m];
+        for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = n == 0 ? 0.0f : (float)o[m];
     }
 }
 
@@ -198,7 +199,7 @@ __global__ void mg_jacobi_kernel(size_t N, const float *__restrict__ b, const fl
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         float D[9];
 #pragma unroll
-        for (int m = 0; m < 9; ++m) D[m] = Dinv[n * 9 + m];
+        for (int m = 0; m < 9; ++m) D[m] = Dinv[(size_t)m * N + n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             float rv[3];
@@ -230,10 +231,9 @@ __global__ void mg_stencil_apply_kernel(int r, const float *__restrict__ S, cons
         for (int dl = 0; dl < 27; ++dl) {
             const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
             const size_t j = ((size_t)wrap_l(iz + dz, r) * r + wrap_l(iy + dy, r)) * r + wrap_l(ix + dx, r);
-            const float *blk = S + (n * 27 + dl) * 9;
             float B[9];
 #pragma unroll
-            for (int m = 0; m < 9; ++m) B[m] = blk[m];
+            for (int m = 0; m < 9; ++m) B[m] = S[(size_t)(dl * 9 + m) * N + n];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const float x0 = x[(size_t)(3 * k) * N + j], x1 = x[(size_t)(3 * k + 1) * N + j],
@@ -300,6 +300,52 @@ __global__ void mg_prolong_kernel(int rc, const float *__restrict__ xc, float *_
 #pragma unroll
         for (int m = 0; m < 18; ++m) xf[(size_t)m * Nf + i] += acc[m];
     }
+}
+
+// ---- lambda_max(D^-1 A) by power iteration (sets the damping per level) ----
+// Uses the first three planes (one load case).
+__global__ void mg_power_seed_kernel(size_t N, float *x) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < 18 * N; n += (size_t)gridDim.x * blockDim.x) {
+        if (n >= 3 * N) {
+            x[n] = 0.0f;
+            continue;
+        }
+        unsigned h = (unsigned)n * 2654435761u + 0x9e3779b9u;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        x[n] = (float)(h & 0xffffff) / 8388608.0f - 1.0f;
+    }
+}
+
+// y = D^-1 t on planes 0..2 and ||y||^2 (deterministic last-block reduction).
+__global__ void mg_power_dinv_kernel(size_t N, const float *t, const float *Dinv, float *y, double *partial,
+                                     unsigned *ticket, double *out) {
+    double acc[1] = {0.0};
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        float D[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) D[m] = Dinv[(size_t)m * N + n];
+        const float r0 = t[n], r1 = t[N + n], r2 = t[2 * N + n];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float v = D[3 * i] * r0 + D[3 * i + 1] * r1 + D[3 * i + 2] * r2;
+            y[(size_t)i * N + n] = v;
+            acc[0] += (double)v * v;
+        }
+    }
+    block_reduce_store<1>(acc, partial, blockIdx.x);
+    if (!last_block_ticket(ticket, gridDim.x)) return;
+    __shared__ double tot[1];
+    sum_partials_ordered<1>(partial, gridDim.x, tot);
+    if (threadIdx.x == 0) out[0] = tot[0];
+}
+
+// x = y / ||y|| on planes 0..2
+__global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nrm2, float *x) {
+    const float inv = (float)(1.0 / sqrt(nrm2[0] > 0.0 ? nrm2[0] : 1.0));
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < 3 * N; n += (size_t)gridDim.x * blockDim.x)
+        x[n] = y[n] * inv;
 }
 
 // x = Ainv b on the coarsest level (dense, 3N x 3N, applied per load case).

@@ -264,6 +264,42 @@ ApplyArgs<T> make_apply(int r, const Density &den, const ElemOp<T> &op) {
     return a;
 }
 
+// One PCG iteration recorded as a CUDA graph and replayed: the V-cycle alone
+// is ~40 small kernels, whose host launch cost would otherwise dominate.
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;  // kernels per replay
+    ~IterGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+template <typename F>
+inline int capture_iteration(shl_ctx *ctx, cudaStream_t s, IterGraph *g, F &&record) {
+    const unsigned long long l0 = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    SHL_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int rc = record();
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != SHL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return set_err(ctx, SHL_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) return set_err(ctx, SHL_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
+    g->launches = ctx->launches - l0;
+    ctx->launches = l0;
+    return SHL_OK;
+}
+
+inline int replay(shl_ctx *ctx, cudaStream_t s, IterGraph *g, int times) {
+    for (int i = 0; i < times; ++i) SHL_CUDA(ctx, cudaGraphLaunch(g->exec, s));
+    ctx->launches += g->launches * (unsigned long long)times;
+    return SHL_OK;
+}
+
 // Runs PCG from the residual in b.r and the iterate in b.x for the load cases
 // in want.  The device deactivates each case at convergence or st->maxit; the
 // host polls the active count every chunk of iterations.
@@ -286,16 +322,26 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     a.st = st;
     a.ticket = &st->ticket_apply;
     const int chunk = 32;
+    {
+        const int tz = pick_tz(r, 6);
+        const size_t nblk = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * ((r + tz - 1) / tz) * 6;
+        double *ap = nullptr;
+        SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
+        a.partial = ap;
+    }
+    IterGraph graph;
+    SHL_TRY(capture_iteration(ctx, s, &graph, [&]() -> int {
+        SHL_TRY(launch_apply<T>(ctx, a, s));
+        pcg_update_kernel<T><<<gv, kBlk, 0, s>>>(va);
+        pcg_direction_kernel<T><<<gv, kBlk, 0, s>>>(va);
+        ctx->launches += 2;
+        return SHL_OK;
+    }));
+    // the device deactivates every load case by st->maxit; the host cap is a backstop
     const long long cap = (long long)max_iters_backstop + 2 * chunk;
     for (long long it = 0;; it += chunk) {
         if (it > cap) return set_err(ctx, SHL_ENOCONV, "PCG did not stop within %lld iterations", cap);
-        for (int c = 0; c < chunk; ++c) {
-            SHL_TRY(launch_apply<T>(ctx, a, s));
-            pcg_update_kernel<T><<<gv, kBlk, 0, s>>>(va);
-            pcg_direction_kernel<T><<<gv, kBlk, 0, s>>>(va);
-            ctx->launches += 2;
-        }
-        SHL_CUDA(ctx, cudaGetLastError());
+        SHL_TRY(replay(ctx, s, &graph, chunk));
         SHL_CUDA(ctx, cudaMemcpyAsync(host_nactive, &st->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
         SHL_CUDA(ctx, cudaStreamSynchronize(s));
         if (*host_nactive == 0) break;
@@ -346,6 +392,7 @@ inline int host_pinned(shl_ctx *ctx, HostPinned *hp) {
 struct MgLevel {
     int r = 0;
     size_t N = 0;
+    float omega = 0.6f;     // damping, 1.2 / lambda_max(D^-1 A) estimated at setup
     float *S = nullptr;     // stencil (levels >= 1)
     float *Dinv = nullptr;  // 3x3 block-Jacobi inverses
     float *x = nullptr, *b = nullptr, *t = nullptr;
@@ -356,7 +403,6 @@ struct Mg {
     MgLevel lv[kMgMaxLevels];
     float *Ainv = nullptr;  // coarsest dense inverse
     int n3 = 0;
-    float omega = 0.6f;
     int nu = 2;
 };
 
@@ -394,8 +440,7 @@ inline int mg_constants(shl_ctx *ctx, double nu) {
 
 inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opts *o, Mg *mg, cudaStream_t s) {
     SHL_TRY(mg_constants(ctx, o->nu));
-    mg->omega = (float)(o->mg_omega > 0.0 ? o->mg_omega : 0.6);
-    mg->nu = o->mg_nu > 0 ? o->mg_nu : 2;
+    mg->nu = o->mg_nu > 0 ? o->mg_nu : 1;
     char nm[64];
     for (int l = 0; l <= mg->L; ++l) {
         MgLevel &L = mg->lv[l];
@@ -434,6 +479,47 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         ctx->launches += 2;
     }
     SHL_CUDA(ctx, cudaGetLastError());
+    // damping per smoothed level from lambda_max(D^-1 A) (power iteration)
+    {
+        ElemOp<float> op32;
+        SHL_TRY(get_op(ctx, o->nu, r, &op32));
+        double *pw = nullptr, *ppart = nullptr;
+        unsigned *ptick = nullptr;
+        float *py = nullptr;
+        SHL_TRY(ws_get_t(ctx, "mg_pow", 64, &pw));
+        SHL_TRY(ws_get_t(ctx, "mg_pow_partial", (size_t)148 * 8, &ppart));
+        SHL_TRY(ws_get_t(ctx, "mg_pow_ticket", 1, &ptick));
+        SHL_TRY(ws_get_t(ctx, "mg_pow_y", 3 * mg->lv[0].N, &py));
+        const int kPow = 15;
+        for (int l = 0; l < mg->L; ++l) {
+            MgLevel &L = mg->lv[l];
+            float *x = l == 0 ? nullptr : L.x;
+            if (l == 0) SHL_TRY(ws_get_t(ctx, "z32", 18 * L.N, &x));
+            mg_power_seed_kernel<<<grid1d(18 * L.N), kBlk, 0, s>>>(L.N, x);
+            for (int it = 0; it < kPow; ++it) {
+                if (l == 0) {
+                    ApplyArgs<float> a = make_apply<float>(r, den, op32);
+                    a.nvec = 1;
+                    a.p = x;
+                    a.q = L.t;
+                    a.pin = 1;
+                    SHL_TRY(launch_apply<float>(ctx, a, s));
+                } else {
+                    mg_stencil_apply_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, x, L.t, nullptr);
+                }
+                const int g = grid1d(L.N, kBlk, 148 * 8);
+                mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + it);
+                mg_power_scale_kernel<<<grid1d(3 * L.N), kBlk, 0, s>>>(L.N, py, pw + it, x);
+                ctx->launches += 3;
+            }
+            double hpw[kPow];
+            SHL_CUDA(ctx, cudaMemcpyAsync(hpw, pw, sizeof(hpw), cudaMemcpyDeviceToHost, s));
+            SHL_CUDA(ctx, cudaStreamSynchronize(s));
+            const double lam = std::sqrt(hpw[kPow - 1]);
+            const double base = o->mg_omega > 0.0 ? o->mg_omega : 1.4;  // omega * lambda_max
+            L.omega = (float)(lam > 0.0 && std::isfinite(lam) ? base / lam : 0.3);
+        }
+    }
     // coarsest: dense, coarse node 0 pinned, inverted in FP64 on the host
     const MgLevel &C = mg->lv[mg->L];
     const int n3 = (int)(3 * C.N);
@@ -452,7 +538,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             if (I == 0 || J == 0) continue;
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j)
-                    A[(3 * (I - 1) + i) * (size_t)m + 3 * (J - 1) + j] += Sh[(I * 27 + dl) * 9 + 3 * i + j];
+                    A[(3 * (I - 1) + i) * (size_t)m + 3 * (J - 1) + j] += Sh[(size_t)(dl * 9 + 3 * i + j) * C.N + I];
         }
     }
     // symmetrise (FP32 stencil rounding), Cholesky, explicit inverse
@@ -497,7 +583,6 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
 // operator of the matrix-free apply.
 inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const float *b0, float *x0, PcgState *st,
                      cudaStream_t s) {
-    const float w = mg->omega;
     auto apply_level = [&](int l, const float *x, float *t) -> int {
         if (l == 0) {
             ApplyArgs<float> a = fine;
@@ -518,6 +603,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     mg->lv[0].x = x0;
     for (int l = 0; l < mg->L; ++l) {  // down: pre-smooth, restrict the residual
         MgLevel &L = mg->lv[l];
+        const float w = L.omega;
         const int g = grid1d(L.N);
         mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, w, L.x, 1, st);
         ++ctx->launches;
@@ -537,6 +623,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     }
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
         MgLevel &L = mg->lv[l];
+        const float w = L.omega;
         const int g = grid1d(L.N);
         mg_prolong_kernel<<<g, kBlk, 0, s>>>(mg->lv[l + 1].r, mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
         ++ctx->launches;
@@ -624,7 +711,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         SHL_TRY(ws_get_t(ctx, "refine_scale", 8, &one));
         const double h_one[8] = {1, 1, 1, 1, 1, 1, 1, 1};
         SHL_CUDA(ctx, cudaMemcpyAsync(one, h_one, sizeof(h_one), cudaMemcpyHostToDevice, s));
-        const double delta = o->inner_tol > 0.0 ? o->inner_tol : 1e-2;
+        const double delta = o->inner_tol > 0.0 ? o->inner_tol : 1e-3;
         // r64 = f - K x64 (pinned); r32 = float(r64); x32 = 0
         SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
         refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, one, 0x3f, b.r, b.x);
@@ -666,24 +753,35 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             a.dot = 1;
             a.st = st;
             a.ticket = &st->ticket_apply;
-            const int chunk = use_mg ? 4 : 32;
+            const int chunk = use_mg ? 8 : 32;
+            // workspaces the iteration uses must exist before capture
+            {
+                const int tz = pick_tz(r, 6);
+                const size_t nblk = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * ((r + tz - 1) / tz) * 6;
+                double *ap = nullptr;
+                SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
+                a.partial = ap;
+            }
+            auto iteration = [&]() -> int {
+                SHL_TRY(launch_apply<float>(ctx, a, s));
+                pcg_update_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                ++ctx->launches;
+                if (use_mg) {
+                    SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s));
+                    pcg_rz_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                    ++ctx->launches;
+                }
+                pcg_direction_kernel<float><<<gv, kBlk, 0, s>>>(va);
+                ++ctx->launches;
+                return SHL_OK;
+            };
+            IterGraph graph;
+            SHL_TRY(capture_iteration(ctx, s, &graph, iteration));
             PcgState hst;
             for (long long it = 0;; it += chunk) {
                 if (it > (long long)maxit + 2 * chunk)
                     return set_err(ctx, SHL_ENOCONV, "PCG did not stop within %d iterations", maxit);
-                for (int c = 0; c < chunk; ++c) {
-                    SHL_TRY(launch_apply<float>(ctx, a, s));
-                    pcg_update_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                    ++ctx->launches;
-                    if (use_mg) {
-                        SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s));
-                        pcg_rz_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                        ++ctx->launches;
-                    }
-                    pcg_direction_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                    ++ctx->launches;
-                }
-                SHL_CUDA(ctx, cudaGetLastError());
+                SHL_TRY(replay(ctx, s, &graph, chunk));
                 SHL_CUDA(ctx, cudaMemcpyAsync(&hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
                 SHL_CUDA(ctx, cudaStreamSynchronize(s));
                 if (hst.numeric_err) {
@@ -785,7 +883,8 @@ inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
         return set_err(ctx, SHL_EINVAL, "unknown density mode %d", o->density);
     if (o->precond != SHL_PRECOND_JACOBI && o->precond != SHL_PRECOND_MG)
         return set_err(ctx, SHL_EINVAL, "unknown preconditioner %d", o->precond);
-    if (!(o->mg_omega <= 0.0 || o->mg_omega < 2.0)) return set_err(ctx, SHL_EINVAL, "mg_omega must be < 2");
+    if (!(o->mg_omega <= 0.0 || o->mg_omega < 2.0))
+        return set_err(ctx, SHL_EINVAL, "mg_omega (damping times lambda_max) must be < 2");
     return SHL_OK;
 }
 
@@ -805,6 +904,13 @@ inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double
     cudaEventCreate(&e2);
     cudaEventRecord(e0, s);
     int rc = run_solve(ctx, r, den, o, x64, warm, s, &so);
+    if (rc == SHL_OK && so.status == SHL_ENUMERIC && so.precond == SHL_PRECOND_MG) {
+        // multigrid-preconditioned CG broke down: solve again with point Jacobi
+        shl_solve_opts oj = *o;
+        oj.precond = SHL_PRECOND_JACOBI;
+        so = SolveOut();
+        rc = run_solve(ctx, r, den, &oj, x64, false, s, &so);
+    }
     cudaEventRecord(e1, s);
     double *Cd = nullptr;
     if (rc == SHL_OK) rc = ws_get_t(ctx, "chom_out", 36, &Cd);
@@ -1002,10 +1108,10 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->precision = SHL_FP64;
     o->density = SHL_MASK;
     o->kappa = 0.0;
-    o->inner_tol = 1e-2;
+    o->inner_tol = 1e-3;
     o->precond = SHL_PRECOND_MG;
-    o->mg_nu = 2;
-    o->mg_omega = 0.6;
+    o->mg_nu = 1;
+    o->mg_omega = 1.4;
 }
 
 int shl_create(const shl_opts *opts, shl_ctx **out) {
