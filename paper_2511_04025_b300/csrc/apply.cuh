@@ -132,24 +132,54 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         const T *pk = zero_in ? nullptr : a.p + (size_t)(3 * k) * N;
         const size_t rr = (size_t)r * r;
 
+        // Copy descriptors of this thread's share of a node plane, computed once
+        // for the 16-byte path: (component, row, chunk) -> shared offset and
+        // global offset within a z-plane (interior chunks of 16 bytes, wrapped
+        // scalars for the halo).  Ragged tiles and grids that are not a multiple
+        // of the chunk take the scalar path, indexed on the fly.
+        constexpr int NCH = TX / VEC + 2;
+        constexpr int NITEM_V = 3 * NY * NCH;
+        constexpr int MAXIT = (NITEM_V + S::THREADS - 1) / S::THREADS;
+        int dst_off[MAXIT];
+        size_t src_off[MAXIT];
+        int kind[MAXIT];  // 0 none, 1 scalar, 2 sixteen bytes
+#pragma unroll
+        for (int u = 0; u < MAXIT; ++u) {
+            const int idx = tid + u * S::THREADS;
+            kind[u] = 0;
+            dst_off[u] = 0;
+            src_off[u] = 0;
+            if (!vec_ok || zero_in || idx >= NITEM_V) continue;
+            const int c = idx / (NY * NCH), rem = idx - c * (NY * NCH);
+            const int ly = rem / NCH, ch = rem - ly * NCH;
+            const size_t row = (size_t)c * N + (size_t)wrapi(y0 - 1 + ly, r) * r;
+            const int drow = (c * NY + ly) * PITCH + OFF;
+            if (ch == 0) {
+                kind[u] = 1;
+                dst_off[u] = drow;
+                src_off[u] = row + wrapi(x0 - 1, r);
+            } else if (ch == NCH - 1) {
+                kind[u] = 1;
+                dst_off[u] = drow + TX + 1;
+                src_off[u] = row + wrapi(x0 + TX, r);
+            } else {
+                kind[u] = 2;
+                dst_off[u] = drow + 1 + (ch - 1) * VEC;
+                src_off[u] = row + x0 + (ch - 1) * VEC;
+            }
+        }
         auto load_plane = [&](int z, int slot) {
             if (zero_in) return;
-            const T *base = pk + (size_t)wrapi(z, r) * rr;
+            const int zw = z < 0 ? z + r : (z >= r ? z - r : z);
+            const T *base = pk + (size_t)zw * rr;
             T *dst = sp + slot * PLANE;
             if (vec_ok) {
-                constexpr int NCH = TX / VEC + 2;
-                for (int idx = tid; idx < 3 * NY * NCH; idx += S::THREADS) {
-                    const int c = idx / (NY * NCH), rem = idx - c * (NY * NCH);
-                    const int ly = rem / NCH, ch = rem - ly * NCH;
-                    const int gy = wrapi(y0 - 1 + ly, r);
-                    const T *row = base + (size_t)c * N + (size_t)gy * r;
-                    T *drow = dst + (c * NY + ly) * PITCH + OFF;
-                    if (ch == 0)
-                        cp_async_small<sizeof(T)>(drow, row + wrap_near(x0 - 1, r));
-                    else if (ch == NCH - 1)
-                        cp_async_small<sizeof(T)>(drow + TX + 1, row + wrap_near(x0 + TX, r));
-                    else
-                        cp_async16(drow + 1 + (ch - 1) * VEC, row + x0 + (ch - 1) * VEC);
+#pragma unroll
+                for (int u = 0; u < MAXIT; ++u) {
+                    if (kind[u] == 2)
+                        cp_async16(dst + dst_off[u], base + src_off[u]);
+                    else if (kind[u] == 1)
+                        cp_async_small<sizeof(T)>(dst + dst_off[u], base + src_off[u]);
                 }
             } else {
                 constexpr int NXX = TX + 2;
@@ -206,9 +236,10 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
             }
         }
 
+        const size_t exy = (size_t)ey * r + ex;
         auto modulus = [&](int ez) -> T {
             if (!el) return T(0);
-            const size_t e = ((size_t)wrapi(ez, r) * r + ey) * r + ex;
+            const size_t e = (size_t)(ez < 0 ? ez + r : (ez >= r ? ez - r : ez)) * rr + exy;
             T Ee = a.rho ? (T)(a.Evoid + a.rho[e] * (a.E - a.Evoid)) : (a.mask[e] ? a.E : a.Evoid);
             return RESID ? -Ee : Ee;
         };

@@ -218,9 +218,13 @@ __global__ void mg_jacobi_kernel(size_t N, const float *__restrict__ b, const fl
     }
 }
 
-// t = S x (27-point 3x3-block stencil, periodic).
-__global__ void mg_stencil_apply_kernel(int r, const float *__restrict__ S, const float *__restrict__ x,
-                                        float *__restrict__ t, const PcgState *st) {
+// 27-point 3x3-block stencil (periodic) with a fused epilogue:
+//   mode 0: out = S x
+//   mode 1: out = b - S x                      (residual)
+//   mode 2: out = x + w D^-1 (b - S x)         (one damped block-Jacobi sweep)
+__global__ void mg_stencil_kernel(int r, const float *__restrict__ S, const float *__restrict__ x,
+                                  const float *__restrict__ b, const float *__restrict__ Dinv, float w, int mode,
+                                  float *__restrict__ out, const PcgState *st) {
     if (mg_done(st)) return;
     const size_t N = (size_t)r * r * r;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
@@ -242,12 +246,33 @@ __global__ void mg_stencil_apply_kernel(int r, const float *__restrict__ S, cons
                 for (int i = 0; i < 3; ++i) acc[3 * k + i] += B[3 * i] * x0 + B[3 * i + 1] * x1 + B[3 * i + 2] * x2;
             }
         }
+        if (mode == 0) {
 #pragma unroll
-        for (int m = 0; m < 18; ++m) t[(size_t)m * N + n] = acc[m];
+            for (int m = 0; m < 18; ++m) out[(size_t)m * N + n] = acc[m];
+        } else if (mode == 1) {
+#pragma unroll
+            for (int m = 0; m < 18; ++m) out[(size_t)m * N + n] = b[(size_t)m * N + n] - acc[m];
+        } else {
+            float D[9];
+#pragma unroll
+            for (int m = 0; m < 9; ++m) D[m] = Dinv[(size_t)m * N + n];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float rv[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) rv[i] = b[(size_t)(3 * k + i) * N + n] - acc[3 * k + i];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const size_t o = (size_t)(3 * k + i) * N + n;
+                    out[o] = x[o] + w * (D[3 * i] * rv[0] + D[3 * i + 1] * rv[1] + D[3 * i + 2] * rv[2]);
+                }
+            }
+        }
     }
 }
 
-// bc = R (bf - tf): coarse I gathers w(a) (bf - tf)[2I + a].
+// bc = R (bf - tf): coarse I gathers w(a) (bf - tf)[2I + a]; tf may be null
+// (bf is then the residual itself).
 __global__ void mg_restrict_kernel(int rc, const float *__restrict__ bf, const float *__restrict__ tf,
                                    float *__restrict__ bc, const PcgState *st) {
     if (mg_done(st)) return;
@@ -265,8 +290,13 @@ __global__ void mg_restrict_kernel(int rc, const float *__restrict__ bf, const f
                     const float w = tri_w(ax, ay, az);
                     const size_t f =
                         ((size_t)wrap_l(2 * iz + az, rf) * rf + wrap_l(2 * iy + ay, rf)) * rf + wrap_l(2 * ix + ax, rf);
+                    if (tf) {
 #pragma unroll
-                    for (int m = 0; m < 18; ++m) acc[m] += w * (bf[(size_t)m * Nf + f] - tf[(size_t)m * Nf + f]);
+                        for (int m = 0; m < 18; ++m) acc[m] += w * (bf[(size_t)m * Nf + f] - tf[(size_t)m * Nf + f]);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 18; ++m) acc[m] += w * bf[(size_t)m * Nf + f];
+                    }
                 }
 #pragma unroll
         for (int m = 0; m < 18; ++m) bc[(size_t)m * Nc + I] = acc[m];

@@ -34,19 +34,26 @@ __global__ void pcg_update_kernel(VecArgs<T> a) {
     }
     DotAcc<T> dacc[12];
     const size_t N = a.N;
+    // the vectors never alias: lets the loads of all planes be issued together
+    T *__restrict__ x = a.x;
+    T *__restrict__ rv_ = a.r;
+    const T *__restrict__ p = a.p;
+    const T *__restrict__ q = a.q;
+    const T *__restrict__ dinv = a.dinv;
+    const bool zmode = a.z != nullptr;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const T di = a.z ? T(0) : a.dinv[n];
+        const T di = zmode ? T(0) : dinv[n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             if (!act[k]) continue;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
-                const T pv = a.p[o], qv = a.q[o];
-                a.x[o] += al[k] * pv;
-                const T rv = a.r[o] - al[k] * qv;
-                a.r[o] = rv;
-                if (!a.z) dacc[k].add(rv * (di * rv));
+                const T pv = p[o], qv = q[o];
+                x[o] += al[k] * pv;
+                const T rv = rv_[o] - al[k] * qv;
+                rv_[o] = rv;
+                if (!zmode) dacc[k].add(rv * (di * rv));
                 dacc[6 + k].add(rv * rv);
             }
         }
@@ -100,7 +107,7 @@ __global__ void pcg_rz_kernel(VecArgs<T> a) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
-                dacc[k].add(a.r[o] * a.z[o]);
+                dacc[k].add(__ldg(a.r + o) * __ldg(a.z + o));
             }
         }
     }
@@ -173,15 +180,19 @@ __global__ void pcg_direction_kernel(VecArgs<T> a) {
         be[k] = (T)st->beta[k];
     }
     const size_t N = a.N;
+    T *__restrict__ p = a.p;
+    const T *__restrict__ r = a.r;
+    const T *__restrict__ z = a.z;
+    const T *__restrict__ dinv = a.dinv;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const T di = a.z ? T(0) : a.dinv[n];
+        const T di = z ? T(0) : dinv[n];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             if (!act[k]) continue;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
-                a.p[o] = (a.z ? a.z[o] : di * a.r[o]) + be[k] * a.p[o];
+                p[o] = (z ? z[o] : di * r[o]) + be[k] * p[o];
             }
         }
     }

@@ -396,6 +396,7 @@ struct MgLevel {
     float *S = nullptr;     // stencil (levels >= 1)
     float *Dinv = nullptr;  // 3x3 block-Jacobi inverses
     float *x = nullptr, *b = nullptr, *t = nullptr;
+    float *xa = nullptr, *xb = nullptr;  // ping-pong iterate buffers (levels >= 1)
 };
 
 struct Mg {
@@ -452,7 +453,10 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             snprintf(nm, sizeof(nm), "mg_S%d", l);
             SHL_TRY(ws_get_t(ctx, nm, L.N * 27 * 9, &L.S));
             snprintf(nm, sizeof(nm), "mg_x%d", l);
-            SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.x));
+            SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.xa));
+            snprintf(nm, sizeof(nm), "mg_y%d", l);
+            SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.xb));
+            L.x = L.xa;
             snprintf(nm, sizeof(nm), "mg_b%d", l);
             SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.b));
         }
@@ -505,7 +509,8 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     a.pin = 1;
                     SHL_TRY(launch_apply<float>(ctx, a, s));
                 } else {
-                    mg_stencil_apply_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, x, L.t, nullptr);
+                    mg_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, x, nullptr, nullptr, 1.0f, 0, L.t,
+                                                                  nullptr);
                 }
                 const int g = grid1d(L.N, kBlk, 148 * 8);
                 mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + it);
@@ -580,40 +585,48 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
 }
 
 // z = V-cycle(b) for the pinned fine system; `fine` carries the density and
-// operator of the matrix-free apply.
+// operator of the matrix-free apply.  Coarse levels use the fused stencil
+// kernel (residual, or a full Jacobi sweep into the other ping-pong buffer).
 inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const float *b0, float *x0, PcgState *st,
                      cudaStream_t s) {
-    auto apply_level = [&](int l, const float *x, float *t) -> int {
-        if (l == 0) {
-            ApplyArgs<float> a = fine;
-            a.p = x;
-            a.q = t;
-            a.pin = 1;
-            a.dot = 0;
-            a.resid = 0;
-            a.st = st;
-            return launch_apply<float>(ctx, a, s);
-        }
-        const MgLevel &L = mg->lv[l];
-        mg_stencil_apply_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, x, t, st);
+    auto fine_apply = [&](const float *x, float *t) -> int {
+        ApplyArgs<float> a = fine;
+        a.p = x;
+        a.q = t;
+        a.pin = 1;
+        a.dot = 0;
+        a.resid = 0;
+        a.st = st;
+        return launch_apply<float>(ctx, a, s);
+    };
+    auto sweep = [&](MgLevel &L, int mode) {  // coarse level: mode 1 residual into t, mode 2 Jacobi sweep
+        float *out = mode == 1 ? L.t : (L.x == L.xa ? L.xb : L.xa);
+        mg_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, L.x, L.b, L.Dinv, L.omega, mode, out, st);
         ++ctx->launches;
-        return SHL_OK;
+        if (mode == 2) L.x = out;
     };
     mg->lv[0].b = const_cast<float *>(b0);
     mg->lv[0].x = x0;
+    for (int l = 1; l <= mg->L; ++l) mg->lv[l].x = mg->lv[l].xa;
     for (int l = 0; l < mg->L; ++l) {  // down: pre-smooth, restrict the residual
         MgLevel &L = mg->lv[l];
-        const float w = L.omega;
         const int g = grid1d(L.N);
-        mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, w, L.x, 1, st);
+        mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
         ++ctx->launches;
-        for (int it = 1; it < mg->nu; ++it) {
-            SHL_TRY(apply_level(l, L.x, L.t));
-            mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, w, L.x, 0, st);
-            ++ctx->launches;
+        if (l == 0) {
+            for (int it = 1; it < mg->nu; ++it) {
+                SHL_TRY(fine_apply(L.x, L.t));
+                mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
+                ++ctx->launches;
+            }
+            SHL_TRY(fine_apply(L.x, L.t));
+            mg_restrict_kernel<<<grid1d(mg->lv[1].N), kBlk, 0, s>>>(mg->lv[1].r, L.b, L.t, mg->lv[1].b, st);
+        } else {
+            for (int it = 1; it < mg->nu; ++it) sweep(L, 2);
+            sweep(L, 1);
+            mg_restrict_kernel<<<grid1d(mg->lv[l + 1].N), kBlk, 0, s>>>(mg->lv[l + 1].r, L.t, nullptr,
+                                                                         mg->lv[l + 1].b, st);
         }
-        SHL_TRY(apply_level(l, L.x, L.t));
-        mg_restrict_kernel<<<grid1d(mg->lv[l + 1].N), kBlk, 0, s>>>(mg->lv[l + 1].r, L.b, L.t, mg->lv[l + 1].b, st);
         ++ctx->launches;
     }
     {
@@ -623,14 +636,17 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     }
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
         MgLevel &L = mg->lv[l];
-        const float w = L.omega;
         const int g = grid1d(L.N);
         mg_prolong_kernel<<<g, kBlk, 0, s>>>(mg->lv[l + 1].r, mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
         ++ctx->launches;
         for (int it = 0; it < mg->nu; ++it) {
-            SHL_TRY(apply_level(l, L.x, L.t));
-            mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, w, L.x, 0, st);
-            ++ctx->launches;
+            if (l == 0) {
+                SHL_TRY(fine_apply(L.x, L.t));
+                mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
+                ++ctx->launches;
+            } else {
+                sweep(L, 2);
+            }
         }
     }
     SHL_CUDA(ctx, cudaGetLastError());
