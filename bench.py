@@ -10,6 +10,8 @@ not available).  Multi-GPU: independent replicas (designs are independent),
 one process per GPU, weak scaling, no data-path collective.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl shl|reference]
+  python bench.py --serve [--requests R] [--slots S]   # serving stream
+  python bench.py --kernel apply [--r R]              # dominant kernel alone
 """
 from __future__ import annotations
 
@@ -34,9 +36,10 @@ WORKLOADS = {
 }
 APPLY_BYTES_PER_NODE_F32 = 72 + 72 + 1  # read p (18 floats), write q (18 floats), 1 mask byte
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes per launch of the FP32 stiffness apply at 64^3 from one ncu
-# capture (profiles/apply_fp32_64.md); None until measured for the current kernel.
-APPLY_TRAFFIC_64 = None
+# DRAM bytes (read + write) per launch of the FP32 stiffness apply at 64^3,
+# from one `ncu --set full` capture of `bench.py --kernel apply --r 64`; reset
+# to None whenever the kernel changes.
+APPLY_TRAFFIC_64 = 19_195_648
 
 
 def peaks():
@@ -174,6 +177,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_apply(h, r, design, stream, launches=40):
+    """Average duration of one FP32 stiffness apply (6 load cases) on the
+    design's mask, CUDA events on the launch stream.  The launches rotate over
+    enough (p, q) pairs that the working set exceeds the 126 MB L2, so every
+    launch streams its operands from HBM."""
+    import torch
+    from paper_2511_04025_b300 import shl
+    N = r ** 3
+    mask = torch.empty(N, dtype=torch.uint8, device="cuda")
+    shl.shl_voxelize(h, design, r, mask=mask, stream=stream)
+    per_set = 2 * 18 * N * 4
+    nsets = max(1, -(-(320 << 20) // per_set))
+    ps = [torch.randn(18, N, dtype=torch.float32, device="cuda") for _ in range(nsets)]
+    qs = [torch.empty_like(p) for p in ps]
+    torch.cuda.synchronize()
+    for i in range(3 * nsets):
+        shl.shl_apply(h, r, ps[i % nsets], qs[i % nsets], mask=mask, stream=stream)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for i in range(launches):
+        shl.shl_apply(h, r, ps[i % nsets], qs[i % nsets], mask=mask, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / 1e3 / launches
+
+
+def apply_roofline(r, apply_s):
+    peak, peak_kind = peaks()
+    achieved = APPLY_BYTES_PER_NODE_F32 * r ** 3 / apply_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": "apply_kernel<float> (stiffness apply)",
+            "peak_kind": peak_kind, "launch_us": apply_s * 1e6, "operands": "HBM (rotating > L2)"}
+
+
+def run_kernel(args):
+    """The dominant kernel alone: FP32 stiffness apply on the workload's first
+    design at grid size --r (default: the workload's)."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    torch.cuda.set_device(0)
+    gen, r0, _ = WORKLOADS[args.workload]
+    r = args.r or r0
+    with shl.Context(0) as ctx:
+        stream = torch.cuda.Stream()
+        apply_s = time_apply(ctx.handle, r, getattr(inputs, gen)(0), stream, launches=args.launches)
+    line = {"kernel": "apply", "r": r, "workload": args.workload, "launches": args.launches,
+            "roofline": apply_roofline(r, apply_s)}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: a Poisson request stream (grids 32^3/64^3/96^3 at
     0.50/0.35/0.15, 8-64 charges, 3-20 % solid, 25 % warm-start follow-ups).
@@ -221,6 +274,9 @@ def run_serve(args):
         return (float(np.percentile(v, 50)), float(np.percentile(v, 99))) if v else (None, None)
 
     ok = all(x["stats"]["status"] == 0 for _, x in res1 + res2)
+    failures = [{"pass": ps, "r": q.r, "status": x["stats"]["status"], "warm": x["warm"], "slot": x["slot"],
+                 "iters_max": max(x["stats"]["iters"]), "relres_max": max(x["stats"]["relres"])}
+                for ps, res in (("burst", res1), ("poisson", res2)) for q, x in res if x["stats"]["status"] != 0]
     p50, p99 = lat(res2)
     p50_64, p99_64 = lat(res2, 64)
     line = {
@@ -232,6 +288,7 @@ def run_serve(args):
         "latency_s": {"p50": p50, "p99": p99, "p50_64": p50_64, "p99_64": p99_64},
         "burst": {"designs_per_s": X, "latency_p50": lat(res1)[0], "latency_p99": lat(res1)[1]},
         "warm_hits": int(sum(1 for _, x in res2 if x["warm"])), "all_converged": ok,
+        "failures": failures[:16],
         "clocks": clk2.summary(), "gpu_launches": int(c1 - c0),
     }
     print(json.dumps(line), flush=True)
@@ -250,9 +307,14 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving workload (Poisson stream) instead of the bench")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--kernel", choices=["apply"], help="time the dominant kernel alone instead of the bench")
+    ap.add_argument("--r", type=int, default=0, help="grid size for --kernel (default: the workload's)")
+    ap.add_argument("--launches", type=int, default=40, help="timed launches for --kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return run_kernel(args)
     if args.serve:
         return run_serve(args)
 
@@ -305,28 +367,10 @@ def main():
     value = world * args.steps / dev_s
     e2e = world * args.steps / wall_s
 
-    # dominant kernel: the FP32 stiffness apply of the inner solves, timed live
-    # on the launch stream on the last design's mask
-    N = r ** 3
-    mask = torch.empty(N, dtype=torch.uint8, device="cuda")
-    shl.shl_voxelize(h, designs[-1], r, mask=mask, stream=stream)
-    p = torch.randn(18, N, dtype=torch.float32, device="cuda")
-    q = torch.empty_like(p)
-    for _ in range(5):
-        shl.shl_apply(h, r, p, q, mask=mask, stream=stream)
-    L = 50
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(L):
-        shl.shl_apply(h, r, p, q, mask=mask, stream=stream)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    apply_s = a0.elapsed_time(a1) / 1e3 / L
-    peak, peak_kind = peaks()
-    achieved = APPLY_BYTES_PER_NODE_F32 * N / apply_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": "apply_kernel<float> (stiffness apply)",
-                "peak_kind": peak_kind, "launch_us": apply_s * 1e6}
+    # dominant kernel: the FP32 stiffness apply of the inner solves, timed on
+    # the launch stream on the last design's mask
+    apply_s = time_apply(h, r, designs[-1], stream)
+    roofline = apply_roofline(r, apply_s)
 
     compare = None
     if not args.no_compare and prec == shl.SHL_FP32_REFINE and rank == 0:

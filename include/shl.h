@@ -155,6 +155,9 @@ typedef struct {
     int64_t n_solid;       /* voxels with d <= t                                   */
     int64_t n_ambiguous;   /* voxels with |d - t| <= 1e-9 t                        */
     float ms_field, ms_rhs, ms_solve, ms_chom; /* stage times (CUDA events)        */
+    int32_t precond;       /* preconditioner of the returned solve: SHL_PRECOND_MG, or
+                              SHL_PRECOND_JACOBI (asked for, grid not coarsenable, or
+                              after a multigrid breakdown)                          */
 } shl_stats;
 
 int shl_create(const shl_opts *opts, shl_ctx **out);

@@ -20,7 +20,7 @@ rest is numpy written step by step from the paper:
   chom         Eq. inv-design: C^H_ij = sum_e (chi^i+u^i_e)^T K_e (chi^j+u^j_e)
   gradient     Eq. chain
 
-Readings where the paper is silent (recorded with the rest in the design doc):
+Readings where the paper is silent:
   * iso-level c generalises the zero level set: solid iff |F-c| <= t |grad F|;
   * t from a volume fraction: the margin rule in ``select_t``;
   * kappa = ln(9) * r: h rises from 10 % to 90 % over two voxels.

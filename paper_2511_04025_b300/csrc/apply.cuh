@@ -261,10 +261,10 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         for (int s = 0; s <= a.tz; ++s) {
             const int ez = z0 - 1 + s;  // element plane; node planes ez (bottom), ez + 1 (top)
             if (ez >= r) break;          // uniform
-            if (s > 0) {
-                cp_async_wait_all();     // node plane ez + 1 has landed
-                __syncthreads();
-            }
+            // node plane ez + 1 has landed, and every thread is done reading
+            // the slot the next copy overwrites (at s = 0: the bottom face)
+            if (s > 0) cp_async_wait_all();
+            __syncthreads();
             const bool more = (s < a.tz) && (ez + 1 < r);
             if (more) load_plane(ez + 2, s & 1);  // slot of node plane ez, already in registers
             const T Ee_next = more ? modulus(ez + 1) : T(0);

@@ -50,6 +50,10 @@ struct shl_ctx {
     std::recursive_mutex mu;  // serialises public calls on one context
     void *serve = nullptr;    // serving scheduler state (serve.cuh)
     unsigned long long launches = 0;  // kernels launched (telemetry)
+    // serving slots: every call runs on `stream`, so workspaces are allocated
+    // and freed stream-ordered there (no device-wide synchronisation, which
+    // would disturb other slots' CUDA-graph captures)
+    bool stream_ordered_alloc = false;
 };
 
 namespace shl {
@@ -86,22 +90,33 @@ inline int set_err(shl_ctx *ctx, int code, const char *fmt, ...) {
 inline int ws_get(shl_ctx *ctx, const std::string &name, size_t bytes, void **out) {
     auto &slot = ctx->ws.slots[name];
     if (slot.second < bytes) {
+        const bool so = ctx->stream_ordered_alloc;
         if (slot.first) {
-            cudaStreamSynchronize(ctx->stream);
-            cudaFree(slot.first);
+            if (so) {
+                cudaFreeAsync(slot.first, ctx->stream);
+            } else {
+                // the old buffer may still be in use on the caller's stream
+                cudaDeviceSynchronize();
+                cudaFree(slot.first);
+            }
         }
         slot.first = nullptr;
         slot.second = 0;
         size_t sz = bytes < 256 ? 256 : bytes;
-        cudaError_t e = cudaMalloc(&slot.first, sz);
+        cudaError_t e = so ? cudaMallocAsync(&slot.first, sz, ctx->stream) : cudaMalloc(&slot.first, sz);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return set_err(ctx, SHL_ENOMEM, "cudaMalloc(%zu) for workspace '%s' failed: %s", sz, name.c_str(),
-                           cudaGetErrorString(e));
+            slot.first = nullptr;
+            return set_err(ctx, SHL_ENOMEM, "device allocation of %zu bytes for workspace '%s' failed: %s", sz,
+                           name.c_str(), cudaGetErrorString(e));
         }
         slot.second = sz;
-        e = cudaMemset(slot.first, 0, sz);
-        if (e != cudaSuccess) return set_err(ctx, SHL_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+        // zero-fill ordered before any later use on any stream: the context's
+        // stream is synchronised (a legacy-stream memset would not be ordered
+        // with the non-blocking streams the work runs on)
+        e = cudaMemsetAsync(slot.first, 0, sz, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return set_err(ctx, SHL_ECUDA, "workspace zero-fill: %s", cudaGetErrorString(e));
     }
     *out = slot.first;
     return SHL_OK;
@@ -117,7 +132,13 @@ inline int ws_get_t(shl_ctx *ctx, const std::string &name, size_t count, T **out
 
 inline void ws_free_all(shl_ctx *ctx) {
     for (auto &kv : ctx->ws.slots)
-        if (kv.second.first) cudaFree(kv.second.first);
+        if (kv.second.first) {
+            if (ctx->stream_ordered_alloc)
+                cudaFreeAsync(kv.second.first, ctx->stream);
+            else
+                cudaFree(kv.second.first);
+        }
+    if (ctx->stream_ordered_alloc) cudaStreamSynchronize(ctx->stream);
     ctx->ws.slots.clear();
 }
 

@@ -28,7 +28,6 @@ namespace shl {
 constexpr int kMgMaxLevels = 10;
 constexpr int kMgMaxCoarse = 216;  // nodes of the coarsest level (dense inverse on the host)
 
-__constant__ float c_child_M[8][24][24];  // P_c^T K_unit P_c (unit modulus, unit element)
 
 // Trilinear weight of a fine-node offset v (in fine cells) from a coarse node.
 __host__ __device__ inline float tri_w(int vx, int vy, int vz) {
@@ -80,8 +79,10 @@ __device__ inline int wrap_l(int v, int r) { return v < 0 ? v + r : (v >= r ? v 
 __device__ inline bool mg_done(const PcgState *st) { return st && st->nactive == 0; }
 
 // Level 1 stencil from the fine elements.  Thread = (coarse node I, offset delta).
+// Mc: the 8 child matrices P_c^T K_unit P_c (unit modulus, unit element),
+// [8][24][24] floats in device memory (per context, uploaded at setup).
 __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const double *rho, float E, float Ev, float h,
-                                        float *S) {
+                                        const float *__restrict__ Mc, float *S) {
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27; t += (size_t)gridDim.x * blockDim.x) {
@@ -102,7 +103,7 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) acc[3 * i + j] += Ee * c_child_M[c][3 * A + i][3 * B + j];
+                    for (int j = 0; j < 3; ++j) acc[3 * i + j] += Ee * __ldg(Mc + (c * 24 + 3 * A + i) * 24 + 3 * B + j);
             }
         }
 #pragma unroll

@@ -201,6 +201,7 @@ inline int serve_start(shl_ctx *ctx, Server **out) {
     for (int i = 0; i < slots; ++i) {
         shl_ctx *w = new shl_ctx();
         w->device = ctx->device;
+        w->stream_ordered_alloc = true;
         if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
             delete w;
             break;
@@ -228,7 +229,8 @@ inline void serve_stop(shl_ctx *ctx) {
     }
     sv->cv_work.notify_all();
     for (auto &t : sv->threads) t.join();
-    for (auto &kv : sv->warm) cudaFree(kv.second.x);
+    for (auto &kv : sv->warm) cudaFreeAsync(kv.second.x, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     for (auto *w : sv->slot_ctx) {
         cudaStreamSynchronize(w->stream);
         ws_free_all(w);

@@ -9,6 +9,7 @@
 #include "mg.cuh"
 
 #include <atomic>
+#include <functional>
 
 using namespace shl;
 
@@ -37,6 +38,24 @@ void apply_smem_attr() {
     cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)ApplyShape<T, kTX, kTY>::smem());
     done.fetch_or(bit, std::memory_order_release);
+}
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The limit is a per-function attribute shared by every
+// thread, so it only ever grows: a concurrent launch that needs less is never
+// refused because another thread lowered it.
+inline void raise_smem_limit(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> cur;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &c = cur[{fn, dev}];
+    if (bytes <= c) return;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+        c = bytes;
+    else
+        cudaGetLastError();
 }
 
 // z-extent of a CTA's tile: long enough to amortise the halo plane, short
@@ -134,7 +153,7 @@ inline int run_field(shl_ctx *ctx, const shl_design *d, int r, double *F, double
     while (lines > 4 && (size_t)r * ((r + lines - 1) / lines) < 4 * 148) lines = (lines + 1) / 2;
     FieldArgs fa{r, d->K, lines, d->iso, A, F, gF, dd};
     const size_t smem = field_smem_bytes(r, d->K, lines);
-    cudaFuncSetAttribute(field_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void *)field_grid_kernel, smem);
     field_grid_kernel<<<dim3(r, (r + lines - 1) / lines), 256, smem, s>>>(fa);
     ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
@@ -269,32 +288,54 @@ ApplyArgs<T> make_apply(int r, const Density &den, const ElemOp<T> &op) {
 struct IterGraph {
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches = 0;  // kernels per replay
+    std::function<int()> direct;      // fallback: launch the iteration's kernels
     ~IterGraph() {
         if (exec) cudaGraphExecDestroy(exec);
     }
 };
 
+// Records one iteration; if capture or instantiation fails, the iteration is
+// replayed by launching its kernels directly (same work, more host time).
 template <typename F>
 inline int capture_iteration(shl_ctx *ctx, cudaStream_t s, IterGraph *g, F &&record) {
+    g->direct = [record]() mutable { return record(); };
     const unsigned long long l0 = ctx->launches;
     cudaGraph_t graph = nullptr;
-    SHL_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return SHL_OK;
+    }
     const int rc = record();
     const cudaError_t e = cudaStreamEndCapture(s, &graph);
-    if (rc != SHL_OK) {
+    const unsigned long long per_iter = ctx->launches - l0;
+    ctx->launches = l0;
+    if (e != cudaSuccess || !graph) {
+        // capture invalidated (e.g. by another thread's synchronising call):
+        // clear the sticky capture error and launch the kernels directly
         if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return SHL_OK;
+    }
+    if (rc != SHL_OK) {
+        cudaGraphDestroy(graph);
         return rc;
     }
-    if (e != cudaSuccess) return set_err(ctx, SHL_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
     const cudaError_t e2 = cudaGraphInstantiate(&g->exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e2 != cudaSuccess) return set_err(ctx, SHL_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
-    g->launches = ctx->launches - l0;
-    ctx->launches = l0;
+    if (e2 != cudaSuccess) {
+        cudaGetLastError();
+        g->exec = nullptr;
+        return SHL_OK;
+    }
+    g->launches = per_iter;
     return SHL_OK;
 }
 
 inline int replay(shl_ctx *ctx, cudaStream_t s, IterGraph *g, int times) {
+    if (!g->exec) {
+        for (int i = 0; i < times; ++i) SHL_TRY(g->direct());
+        return SHL_OK;
+    }
     for (int i = 0; i < times; ++i) SHL_CUDA(ctx, cudaGraphLaunch(g->exec, s));
     ctx->launches += g->launches * (unsigned long long)times;
     return SHL_OK;
@@ -423,24 +464,21 @@ inline bool mg_plan(int r, Mg *mg) {
     return true;
 }
 
-inline int mg_constants(shl_ctx *ctx, double nu) {
-    static std::mutex mu;
-    static std::map<std::pair<int, double>, bool> done;  // (device, nu) uploaded
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lk(mu);
-    if (done.count({dev, nu})) return SHL_OK;
-    static float Mc[8][24][24];
+// The 8 child matrices for Poisson ratio nu, uploaded into this context's
+// workspace on stream s (a per-context copy: concurrent contexts may use
+// different nu).
+inline int mg_child_matrices(shl_ctx *ctx, double nu, cudaStream_t s, float **out) {
+    static thread_local float Mc[8][24][24];
     const double err = build_child_matrices(nu, Mc);
     if (!(err < 1e-12)) return set_err(ctx, SHL_EINVAL, "child matrices do not sum to the coarse element (%g)", err);
-    done.clear();  // the constant bank holds one Poisson ratio per device at a time
-    SHL_CUDA(ctx, cudaMemcpyToSymbol(c_child_M, Mc, sizeof(Mc)));
-    done[{dev, nu}] = true;
+    SHL_TRY(ws_get_t(ctx, "mg_childM", (size_t)8 * 24 * 24, out));
+    SHL_CUDA(ctx, cudaMemcpyAsync(*out, Mc, sizeof(Mc), cudaMemcpyHostToDevice, s));
     return SHL_OK;
 }
 
 inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opts *o, Mg *mg, cudaStream_t s) {
-    SHL_TRY(mg_constants(ctx, o->nu));
+    float *childM = nullptr;
+    SHL_TRY(mg_child_matrices(ctx, o->nu, s, &childM));
     mg->nu = o->mg_nu > 0 ? o->mg_nu : 1;
     char nm[64];
     for (int l = 0; l <= mg->L; ++l) {
@@ -476,7 +514,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         const int g = grid1d(L.N * 27, kBlk, 148 * 16);
         if (l == 1)
             mg_galerkin_fine_kernel<<<g, kBlk, 0, s>>>(L.r, den.mask, den.rho, (float)den.E, (float)den.Ev,
-                                                       (float)(1.0 / r), L.S);
+                                                       (float)(1.0 / r), childM, L.S);
         else
             mg_galerkin_coarse_kernel<<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S);
         mg_dinv_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.N, L.S, L.Dinv);
@@ -880,7 +918,7 @@ inline int run_chom(shl_ctx *ctx, int r, const Density &den, double nu, const do
     a.C = C_dev;
     a.op = op;
     const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
-    cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void *)chom_kernel, smem);
     chom_kernel<<<g, kChomThreads, smem, s>>>(a);
     ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
@@ -940,6 +978,7 @@ inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double
             st->relres[k] = so.relres[k];
         }
         st->n_refine = so.n_refine;
+        st->precond = so.precond;
         st->status = rc != SHL_OK ? rc : so.status;
         cudaEventElapsedTime(&st->ms_solve, e0, e1);
         cudaEventElapsedTime(&st->ms_chom, e1, e2);
@@ -1047,7 +1086,7 @@ inline int grad_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_o
         a.g = g;
         a.op = op;
         const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
-        cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)chom_kernel, smem);
         chom_kernel<<<grid1d(N, kChomThreads, 148 * 8), kChomThreads, smem, s>>>(a);
         ++ctx->launches;
     }
@@ -1060,10 +1099,10 @@ inline int grad_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_o
     ++ctx->launches;
     // back through the separable field to the coefficient tensor and the charges
     const size_t smp = sizeof(double) * ((size_t)r * nb + (size_t)r * 3 * nb);
-    cudaFuncSetAttribute(adj_plane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+    raise_smem_limit((const void *)adj_plane_kernel, smp);
     adj_plane_kernel<<<r, 256, smp, s>>>(r, d->K, F, gF, QR);
     const size_t smc = sizeof(double) * (size_t)r * nb;
-    cudaFuncSetAttribute(adj_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    raise_smem_limit((const void *)adj_coef_kernel, smc);
     adj_coef_kernel<<<1, 512, smc, s>>>(r, d->K, QR, Abar);
     Uploaded up;
     SHL_TRY(upload_design(ctx, d, s, &up, "grad"));
@@ -1398,7 +1437,7 @@ extern "C" int shl_chom_noalloc(int32_t r, const uint8_t *mask_dev, const double
     // the ticket must start at zero; the partials are fully overwritten
     SHL_CUDA(nullptr, cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s));
     const size_t smem = sizeof(double) * 6 * 24 * kChomThreads;
-    SHL_CUDA(nullptr, cudaFuncSetAttribute(chom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    raise_smem_limit((const void *)chom_kernel, smem);
     chom_kernel<<<g, kChomThreads, smem, s>>>(a);
     SHL_CUDA(nullptr, cudaGetLastError());
     return SHL_OK;

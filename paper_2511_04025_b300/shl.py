@@ -50,12 +50,13 @@ class shl_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32 * 6), ("relres", ctypes.c_double * 6), ("n_refine", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("t", ctypes.c_double), ("margin", ctypes.c_double),
                 ("n_solid", ctypes.c_int64), ("n_ambiguous", ctypes.c_int64), ("ms_field", ctypes.c_float),
-                ("ms_rhs", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_chom", ctypes.c_float)]
+                ("ms_rhs", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_chom", ctypes.c_float),
+                ("precond", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return dict(iters=list(self.iters), relres=list(self.relres), n_refine=self.n_refine, status=self.status,
                     t=self.t, margin=self.margin, n_solid=self.n_solid, n_ambiguous=self.n_ambiguous,
-                    ms_field=self.ms_field, ms_solve=self.ms_solve, ms_chom=self.ms_chom)
+                    ms_field=self.ms_field, ms_solve=self.ms_solve, ms_chom=self.ms_chom, precond=self.precond)
 
 
 class shl_request(ctypes.Structure):

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C-ABI.
 
-Tolerances (derived in the design doc):
+Tolerances (derived from the arithmetic of each side):
   * field F, grad F: FP64 on both sides, different summation orders ->
     |dF| <= 1e-12 max|F|;
   * mask: bit-exact (t sits mid-gap; the ambiguous count must be 0);

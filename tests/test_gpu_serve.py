@@ -93,3 +93,52 @@ def test_cancel_unknown_and_invalid(gpu):
         with pytest.raises(shl.ShlError) as e:
             shl.shl_serve_submit(c.handle, d.copy(vf=None), 32, _opts())
         assert e.value.status == shl.SHL_EINVAL
+
+
+def test_concurrent_requests_bitwise_equal_sequential(gpu):
+    """Mixed grid sizes served concurrently (8 slots, twice) give bitwise the
+    same C^H and iteration counts as the same designs solved one at a time: no
+    kernel may depend on what else runs on the SMs or on a slot's history."""
+    designs = [(inputs.random_design(300 + i, 8 + 2 * i, 0.04 + 0.01 * (i % 8)), (32, 24, 48, 16)[i % 4])
+               for i in range(16)]
+    ref = []
+    with shl.Context(0) as c:
+        for d, r in designs:
+            ref.append(shl.shl_homogenize(c.handle, d, r, _opts()))
+    for _ in range(2):
+        with shl.Context(0, max_batch=8) as c:
+            ts = [shl.shl_serve_submit(c.handle, d, r, _opts()) for d, r in designs]
+            res = [shl.shl_serve_wait(c.handle, t) for t in ts]
+        for (C, st), x in zip(ref, res):
+            assert x["stats"]["status"] == 0
+            assert x["stats"]["iters"] == st["iters"]
+            assert np.array_equal(x["C"], C)
+
+
+def test_fresh_contexts_on_threads_agree(gpu):
+    """Fresh contexts used at once from several host threads, each on its own
+    non-blocking stream: workspaces are zeroed before any stream uses them."""
+    import threading
+    d, r = inputs.random_design(11, 16, 0.1), 32
+    with shl.Context(0) as c:
+        Cref, stref = shl.shl_homogenize(c.handle, d, r, _opts())
+    ctxs = [shl.Context(0) for _ in range(8)]
+    out = [None] * len(ctxs)
+
+    def run(j):
+        try:
+            out[j] = shl.shl_homogenize(ctxs[j].handle, d, r, _opts(), stream=torch.cuda.Stream())
+        except Exception as e:  # reported below
+            out[j] = e
+
+    th = [threading.Thread(target=run, args=(j,)) for j in range(len(ctxs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for c in ctxs:
+        c.close()
+    for o in out:
+        assert not isinstance(o, Exception), o
+        C, st = o
+        assert st["iters"] == stref["iters"] and np.array_equal(C, Cref)
