@@ -41,7 +41,7 @@ struct PcgState {
 
 template <typename T>
 struct ApplyArgs {
-    int r, tz, nvec;
+    int r, zc, nvec;  // zc: z chunks of the grid (near-equal heights)
     size_t N;
     const T *p;
     T *q;
@@ -51,6 +51,7 @@ struct ApplyArgs {
     int pin;               // zero the output at node 0
     int resid;             // output -sum_e E_e Khat (p_e + chi^k)
     int dot;               // 0: none, 1: sum p.q, 2: sum q.q (per load case)
+    int defer;             // with dot: only write the per-CTA partials (no grid reduction here)
     double *partial;       // [nblocks][6]
     unsigned *ticket;      // last-block counter
     double *dot_out;       // 6 sums (may be null)
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         const bool el = tid < NT;
         const int exl = el ? tid % EX : 0, eyl = el ? tid / EX : 0;
         const int tiles_x = (r + TX - 1) / TX;
-        const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY, z0 = blockIdx.y * a.tz;
+        const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+        const int z0 = (int)(((long long)blockIdx.y * r) / a.zc), tz = (int)(((long long)(blockIdx.y + 1) * r) / a.zc) - z0;
         const int ex = wrapi(x0 - 1 + exl, r), ey = wrapi(y0 - 1 + eyl, r);
         const int nx = x0 - 1 + exl, ny = y0 - 1 + eyl;
         const bool out_col = el && exl >= 1 && eyl >= 1 && nx < r && ny < r;
@@ -258,14 +260,14 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         if (el) face(0, ftb, own_b);
         T Ee = modulus(z0 - 1);
 
-        for (int s = 0; s <= a.tz; ++s) {
+        for (int s = 0; s <= tz; ++s) {
             const int ez = z0 - 1 + s;  // element plane; node planes ez (bottom), ez + 1 (top)
             if (ez >= r) break;          // uniform
             // node plane ez + 1 has landed, and every thread is done reading
             // the slot the next copy overwrites (at s = 0: the bottom face)
             if (s > 0) cp_async_wait_all();
             __syncthreads();
-            const bool more = (s < a.tz) && (ez + 1 < r);
+            const bool more = (s < tz) && (ez + 1 < r);
             if (more) load_plane(ez + 2, s & 1);  // slot of node plane ez, already in registers
             const T Ee_next = more ? modulus(ez + 1) : T(0);
             T own_t[3];
@@ -345,11 +347,12 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
     if (!a.dot) return;
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    double dsum[6];
+    double dcase[6];
     const double mine = dacc.get();
 #pragma unroll
-    for (int kk = 0; kk < 6; ++kk) dsum[kk] = (kk == k) ? mine : 0.0;
-    block_reduce_store<6>(dsum, a.partial, bid);
+    for (int kk = 0; kk < 6; ++kk) dcase[kk] = (kk == k) ? mine : 0.0;
+    block_reduce_store<6>(dcase, a.partial, bid);
+    if (a.defer) return;  // the consumer reduces the per-CTA partials itself
     if (!last_block_ticket(a.ticket, nblocks)) return;
     __shared__ double tot[6];
     sum_partials_ordered<6>(a.partial, nblocks, tot);

@@ -6,8 +6,8 @@
 // Levels l = 0 (fine, r) .. L (coarsest), r_{l+1} = r_l / 2 while r_l is
 // even and >= 6.  Prolongation P is trilinear interpolation, restriction
 // R = P^T.  Coarse operators are Galerkin, A_{l+1} = P^T A_l P, stored as
-// 27-point stencils of 3x3 blocks (S[I][delta][i][j], delta = (dz+1)*9 +
-// (dy+1)*3 + (dx+1)):
+// 27-point stencils of 3x3 blocks, node-major (S[I][delta][i][j], delta =
+// (dz+1)*9 + (dy+1)*3 + (dx+1); one node's 243 entries are contiguous):
 //   level 1 from the fine elements: a coarse element's matrix is
 //     sum_c E_c P_c^T Khat P_c over its 8 children c, with the 8 child
 //     matrices M_c = P_c^T K_unit P_c precomputed (sum_c M_c = 2 K_unit: the
@@ -107,7 +107,7 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
             }
         }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) S[(size_t)(dl * 9 + m) * Nc + I] = h * acc[m];
+        for (int m = 0; m < 9; ++m) S[(I * 27 + dl) * 9 + m] = h * acc[m];
     }
 }
 
@@ -115,7 +115,6 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
 __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc) {
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
-    const size_t Nf = (size_t)rf * rf * rf;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27; t += (size_t)gridDim.x * blockDim.x) {
         const size_t I = t / 27;
         const int dl = (int)(t % 27);
@@ -136,11 +135,11 @@ __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, 
                                 const float w = wa * wb;
                                 const int bl = (bz + 1) * 9 + (by + 1) * 3 + (bx + 1);
 #pragma unroll
-                                for (int m = 0; m < 9; ++m) acc[m] += w * Sf[(size_t)(bl * 9 + m) * Nf + fi];
+                                for (int m = 0; m < 9; ++m) acc[m] += w * Sf[(fi * 27 + bl) * 9 + m];
                             }
                 }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) Sc[(size_t)(dl * 9 + m) * Nc + I] = acc[m];
+        for (int m = 0; m < 9; ++m) Sc[(I * 27 + dl) * 9 + m] = acc[m];
     }
 }
 
@@ -163,7 +162,7 @@ __device__ inline void inv3(const double a[9], double o[9]) {
 __global__ void mg_dinv_stencil_kernel(size_t N, const float *S, float *Dinv) {
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         double a[9], o[9];
-        for (int m = 0; m < 9; ++m) a[m] = S[(size_t)(13 * 9 + m) * N + n];
+        for (int m = 0; m < 9; ++m) a[m] = S[(n * 27 + 13) * 9 + m];
         inv3(a, o);
         for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = (float)o[m];
     }
@@ -219,117 +218,193 @@ __global__ void mg_jacobi_kernel(size_t N, const float *__restrict__ b, const fl
     }
 }
 
-// 27-point 3x3-block stencil (periodic) with a fused epilogue:
+// Warp reduce-scatter of 18 per-lane values: after five halving steps
+// (offsets 16, 8, 4, 2, 1; 9 + 5 + 3 + 2 + 1 shuffles) each lane holds the
+// warp-wide sum of at most one of the 18 values; rs_id(lane) says which (-1:
+// none).  Every step keeps the first ceil(n/2) positions in the lower lane of
+// a pair and the rest (padded with zeros) in the upper one.
+template <int N, int O>
+__device__ __forceinline__ void rs_step(const float (&v)[N], float (&w)[(N + 1) / 2], bool up) {
+    constexpr int M = (N + 1) / 2;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const float lo = v[q];
+        const float hi = (M + q < N) ? v[(M + q < N) ? M + q : 0] : 0.0f;
+        const float send = up ? lo : hi;
+        const float keep = up ? hi : lo;
+        w[q] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
+__device__ __forceinline__ float reduce_scatter18(const float (&v)[18], int lane) {
+    float a9[9], a5[5], a3[3], a2[2], a1[1];
+    rs_step<18, 16>(v, a9, lane & 16);
+    rs_step<9, 8>(a9, a5, lane & 8);
+    rs_step<5, 4>(a5, a3, lane & 4);
+    rs_step<3, 2>(a3, a2, lane & 2);
+    rs_step<2, 1>(a2, a1, lane & 1);
+    return a1[0];
+}
+
+__device__ __forceinline__ int rs_id(int lane) {
+    int lo = 0, cnt = 18, n = 18;
+    for (int o = 16; o > 0; o >>= 1) {
+        const int m = (n + 1) / 2;
+        if (lane & o) {
+            lo += m;
+            cnt = cnt > m ? cnt - m : 0;
+        } else {
+            cnt = cnt < m ? cnt : m;
+        }
+        n = m;
+    }
+    return cnt > 0 ? lo : -1;
+}
+
+// 27-point 3x3-block stencil (periodic) with a fused epilogue.  One warp per
+// node: lane dl < 27 takes the offset dl (its 9 stencil entries are part of
+// the node's contiguous 243, so the warp's loads are coalesced) and all six
+// load cases; a reduce-scatter sums the 27 contributions, leaving output
+// component rs_id(lane) (load case id / 3) in that lane.  Every load of a node
+// is issued at once: the coarse levels are small, so latency, not bandwidth,
+// bounds them.
 //   mode 0: out = S x
 //   mode 1: out = b - S x                      (residual)
 //   mode 2: out = x + w D^-1 (b - S x)         (one damped block-Jacobi sweep)
-__global__ void mg_stencil_kernel(int r, const float *__restrict__ S, const float *__restrict__ x,
-                                  const float *__restrict__ b, const float *__restrict__ Dinv, float w, int mode,
-                                  float *__restrict__ out, const PcgState *st) {
+// Load cases that have converged (st->active) are skipped.
+__global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__restrict__ S,
+                                                         const float *__restrict__ x, const float *__restrict__ b,
+                                                         const float *__restrict__ Dinv, float w, int mode,
+                                                         float *__restrict__ out, const PcgState *st) {
     if (mg_done(st)) return;
-    const size_t N = (size_t)r * r * r;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int ix = n % r, iy = (n / r) % r, iz = n / ((size_t)r * r);
+    const unsigned N = (unsigned)r * r * r;
+    const int lane = threadIdx.x & 31;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    bool act[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) act[k] = !st || st->active[k] != 0;
+    const bool live = lane < 27;
+    const int dl = live ? lane : 13;
+    const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+    // the output component this lane ends with, its load case, and the lanes
+    // holding the three components of that load case (for the 3x3 Jacobi block)
+    const int myid = rs_id(lane);
+    const int mk = myid >= 0 ? myid / 3 : 0, mi = myid >= 0 ? myid - 3 * mk : 0;
+    int src[3] = {0, 0, 0};
+    bool myact = false;
+#pragma unroll
+    for (int m = 0; m < 18; ++m) {
+        const int owner = __ffs(__ballot_sync(0xffffffffu, myid == m)) - 1;
+        if (m / 3 == mk) src[m % 3] = owner;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (k == mk) myact = act[k] && myid >= 0;
+    for (unsigned n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; n < N; n += nwarps) {
+        const int ix = (int)(n % (unsigned)r), iy = (int)((n / (unsigned)r) % (unsigned)r),
+                  iz = (int)(n / ((unsigned)r * r));
+        const unsigned j = ((unsigned)wrap_l(iz + dz, r) * r + (unsigned)wrap_l(iy + dy, r)) * r + wrap_l(ix + dx, r);
+        float B[9];
+        const float *Sn = S + ((size_t)n * 27 + dl) * 9;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) B[m] = live ? __ldg(Sn + m) : 0.0f;
         float acc[18];
 #pragma unroll
-        for (int m = 0; m < 18; ++m) acc[m] = 0.0f;
-        for (int dl = 0; dl < 27; ++dl) {
-            const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
-            const size_t j = ((size_t)wrap_l(iz + dz, r) * r + wrap_l(iy + dy, r)) * r + wrap_l(ix + dx, r);
-            float B[9];
-#pragma unroll
-            for (int m = 0; m < 9; ++m) B[m] = S[(size_t)(dl * 9 + m) * N + n];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float x0 = x[(size_t)(3 * k) * N + j], x1 = x[(size_t)(3 * k + 1) * N + j],
-                            x2 = x[(size_t)(3 * k + 2) * N + j];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) acc[3 * k + i] += B[3 * i] * x0 + B[3 * i + 1] * x1 + B[3 * i + 2] * x2;
+        for (int k = 0; k < 6; ++k) {
+            float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;
+            if (act[k] && live) {
+                x0 = x[(size_t)(3 * k) * N + j];
+                x1 = x[(size_t)(3 * k + 1) * N + j];
+                x2 = x[(size_t)(3 * k + 2) * N + j];
             }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) acc[3 * k + i] = B[3 * i] * x0 + B[3 * i + 1] * x1 + B[3 * i + 2] * x2;
         }
+        const float own = reduce_scatter18(acc, lane);
+        const size_t o = (size_t)(myid >= 0 ? myid : 0) * N + n;
         if (mode == 0) {
-#pragma unroll
-            for (int m = 0; m < 18; ++m) out[(size_t)m * N + n] = acc[m];
+            if (myact) out[o] = own;
         } else if (mode == 1) {
-#pragma unroll
-            for (int m = 0; m < 18; ++m) out[(size_t)m * N + n] = b[(size_t)m * N + n] - acc[m];
+            if (myact) out[o] = b[o] - own;
         } else {
-            float D[9];
-#pragma unroll
-            for (int m = 0; m < 9; ++m) D[m] = Dinv[(size_t)m * N + n];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                float rv[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) rv[i] = b[(size_t)(3 * k + i) * N + n] - acc[3 * k + i];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const size_t o = (size_t)(3 * k + i) * N + n;
-                    out[o] = x[o] + w * (D[3 * i] * rv[0] + D[3 * i + 1] * rv[1] + D[3 * i + 2] * rv[2]);
-                }
+            const float res = myact ? b[o] - own : 0.0f;
+            const float r0 = __shfl_sync(0xffffffffu, res, src[0]), r1 = __shfl_sync(0xffffffffu, res, src[1]),
+                        r2 = __shfl_sync(0xffffffffu, res, src[2]);
+            if (myact) {
+                const float d0 = __ldg(Dinv + (size_t)(3 * mi) * N + n), d1 = __ldg(Dinv + (size_t)(3 * mi + 1) * N + n),
+                            d2 = __ldg(Dinv + (size_t)(3 * mi + 2) * N + n);
+                out[o] = x[o] + w * (d0 * r0 + d1 * r1 + d2 * r2);
             }
         }
     }
 }
 
-// bc = R (bf - tf): coarse I gathers w(a) (bf - tf)[2I + a]; tf may be null
-// (bf is then the residual itself).
-__global__ void mg_restrict_kernel(int rc, const float *__restrict__ bf, const float *__restrict__ tf,
-                                   float *__restrict__ bc, const PcgState *st) {
+// bc = R (bf - tf): coarse node I gathers w(a) (bf - tf)[2I + a] over its 27
+// fine neighbours; tf may be null (bf is then the residual itself).  Grid:
+// x over coarse nodes (one per thread), y over the 18 planes; converged load
+// cases are skipped.
+__global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *__restrict__ bf,
+                                                          const float *__restrict__ tf, float *__restrict__ bc,
+                                                          const PcgState *st) {
     if (mg_done(st)) return;
-    const size_t Nc = (size_t)rc * rc * rc;
+    const int m = blockIdx.y;
+    if (st && !st->active[m / 3]) return;
+    const unsigned Nc = (unsigned)rc * rc * rc;
     const int rf = 2 * rc;
-    const size_t Nf = (size_t)rf * rf * rf;
-    for (size_t I = blockIdx.x * (size_t)blockDim.x + threadIdx.x; I < Nc; I += (size_t)gridDim.x * blockDim.x) {
-        const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
-        float acc[18];
+    const unsigned rrf = (unsigned)rf * rf;
+    const size_t Nf = (size_t)rrf * rf;
+    const float *bm = bf + (size_t)m * Nf;
+    const float *tm = tf ? tf + (size_t)m * Nf : nullptr;
+    for (unsigned I = blockIdx.x * blockDim.x + threadIdx.x; I < Nc; I += gridDim.x * blockDim.x) {
+        const int ix = (int)(I % (unsigned)rc), iy = (int)((I / (unsigned)rc) % (unsigned)rc),
+                  iz = (int)(I / ((unsigned)rc * rc));
+        const unsigned zo[3] = {(unsigned)wrap_l(2 * iz - 1, rf) * rrf, (unsigned)(2 * iz) * rrf,
+                                (unsigned)wrap_l(2 * iz + 1, rf) * rrf};
+        const unsigned yo[3] = {(unsigned)wrap_l(2 * iy - 1, rf) * rf, (unsigned)(2 * iy) * rf,
+                                (unsigned)wrap_l(2 * iy + 1, rf) * rf};
+        const unsigned xo[3] = {(unsigned)wrap_l(2 * ix - 1, rf), (unsigned)(2 * ix), (unsigned)wrap_l(2 * ix + 1, rf)};
+        float acc = 0.0f;
 #pragma unroll
-        for (int m = 0; m < 18; ++m) acc[m] = 0.0f;
-        for (int az = -1; az <= 1; ++az)
-            for (int ay = -1; ay <= 1; ++ay)
-                for (int ax = -1; ax <= 1; ++ax) {
-                    const float w = tri_w(ax, ay, az);
-                    const size_t f =
-                        ((size_t)wrap_l(2 * iz + az, rf) * rf + wrap_l(2 * iy + ay, rf)) * rf + wrap_l(2 * ix + ax, rf);
-                    if (tf) {
+        for (int az = 0; az < 3; ++az)
 #pragma unroll
-                        for (int m = 0; m < 18; ++m) acc[m] += w * (bf[(size_t)m * Nf + f] - tf[(size_t)m * Nf + f]);
-                    } else {
+            for (int ay = 0; ay < 3; ++ay) {
+                float row = 0.0f;
 #pragma unroll
-                        for (int m = 0; m < 18; ++m) acc[m] += w * bf[(size_t)m * Nf + f];
-                    }
+                for (int ax = 0; ax < 3; ++ax) {
+                    const unsigned f = zo[az] + yo[ay] + xo[ax];
+                    const float v = tm ? bm[f] - tm[f] : bm[f];
+                    row += (ax == 1 ? 1.0f : 0.5f) * v;
                 }
-#pragma unroll
-        for (int m = 0; m < 18; ++m) bc[(size_t)m * Nc + I] = acc[m];
+                acc += (az == 1 ? 1.0f : 0.5f) * (ay == 1 ? 1.0f : 0.5f) * row;
+            }
+        bc[(size_t)m * Nc + I] = acc;
     }
 }
 
-// xf += P xc (trilinear), fine node i from the coarse nodes around it; the
-// fine node 0 (pinned at level 0) is left untouched when pin0 is set.
-__global__ void mg_prolong_kernel(int rc, const float *__restrict__ xc, float *__restrict__ xf, int pin0,
-                                  const PcgState *st) {
+// xf += P xc (trilinear): fine node i takes the coarse nodes around it
+// (odd coordinates average their two coarse neighbours).  Grid: x over fine
+// nodes, y over the 18 planes; converged load cases are skipped; with pin0
+// the fine node 0 (pinned) is left unchanged.
+__global__ void __launch_bounds__(256) mg_prolong_kernel(int rc, const float *__restrict__ xc,
+                                                         float *__restrict__ xf, int pin0, const PcgState *st) {
     if (mg_done(st)) return;
+    const int m = blockIdx.y;
+    if (st && !st->active[m / 3]) return;
     const int rf = 2 * rc;
-    const size_t Nf = (size_t)rf * rf * rf, Nc = (size_t)rc * rc * rc;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < Nf; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned Nf = (unsigned)rf * rf * rf, rrc = (unsigned)rc * rc;
+    const float *xm = xc + (size_t)m * rrc * rc;
+    float *xo = xf + (size_t)m * Nf;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < Nf; i += gridDim.x * blockDim.x) {
         if (pin0 && i == 0) continue;
-        const int fx = i % rf, fy = (i / rf) % rf, fz = i / ((size_t)rf * rf);
+        const int fx = (int)(i % (unsigned)rf), fy = (int)((i / (unsigned)rf) % (unsigned)rf),
+                  fz = (int)(i / ((unsigned)rf * rf));
         const int cx0 = fx >> 1, cy0 = fy >> 1, cz0 = fz >> 1;
-        const int nx = (fx & 1) + 1, ny = (fy & 1) + 1, nz = (fz & 1) + 1;
-        const float wx = (fx & 1) ? 0.5f : 1.0f, wy = (fy & 1) ? 0.5f : 1.0f, wz = (fz & 1) ? 0.5f : 1.0f;
-        float acc[18];
-#pragma unroll
-        for (int m = 0; m < 18; ++m) acc[m] = 0.0f;
-        for (int kz = 0; kz < nz; ++kz)
-            for (int ky = 0; ky < ny; ++ky)
-                for (int kx = 0; kx < nx; ++kx) {
-                    const size_t I = ((size_t)wrap_l(cz0 + kz, rc) * rc + wrap_l(cy0 + ky, rc)) * rc + wrap_l(cx0 + kx, rc);
-                    const float w = wx * wy * wz;
-#pragma unroll
-                    for (int m = 0; m < 18; ++m) acc[m] += w * xc[(size_t)m * Nc + I];
-                }
-#pragma unroll
-        for (int m = 0; m < 18; ++m) xf[(size_t)m * Nf + i] += acc[m];
+        const unsigned cx1 = (fx & 1) ? wrap_l(cx0 + 1, rc) : cx0;
+        const unsigned y0 = (unsigned)cy0 * rc, y1 = (unsigned)((fy & 1) ? wrap_l(cy0 + 1, rc) : cy0) * rc;
+        const unsigned z0 = (unsigned)cz0 * rrc, z1 = (unsigned)((fz & 1) ? wrap_l(cz0 + 1, rc) : cz0) * rrc;
+        const float v = xm[z0 + y0 + cx0] + xm[z0 + y0 + cx1] + xm[z0 + y1 + cx0] + xm[z0 + y1 + cx1] +
+                        xm[z1 + y0 + cx0] + xm[z1 + y0 + cx1] + xm[z1 + y1 + cx0] + xm[z1 + y1 + cx1];
+        xo[i] += 0.125f * v;
     }
 }
 
@@ -379,19 +454,24 @@ __global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nr
         x[n] = y[n] * inv;
 }
 
-// x = Ainv b on the coarsest level (dense, 3N x 3N, applied per load case).
+// x = Ainv b on the coarsest level (dense, 3N x 3N, applied per load case):
+// one warp per (load case, row), lanes split the columns (coalesced row of
+// Ainv), fixed shuffle tree.
 __global__ void mg_dense_solve_kernel(int n3, const float *__restrict__ Ainv, const float *__restrict__ b,
                                       float *__restrict__ x, const PcgState *st) {
     if (mg_done(st)) return;
     const int N = n3 / 3;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 6 * n3; t += gridDim.x * blockDim.x) {
-        const int k = t / n3, row = t % n3;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < 6 * n3; wi += nw) {
+        const int k = wi / n3, row = wi - k * n3;
+        if (st && !st->active[k]) continue;  // warp-uniform
         float s = 0.0f;
-        for (int col = 0; col < n3; ++col) {
-            const int cn = col / 3, ci = col % 3;
-            s += Ainv[(size_t)row * n3 + col] * b[(size_t)(3 * k + ci) * N + cn];
-        }
-        x[(size_t)(3 * k + row % 3) * N + row / 3] = s;
+        for (int col = lane; col < n3; col += 32)
+            s += Ainv[(size_t)row * n3 + col] * b[(size_t)(3 * k + col % 3) * N + col / 3];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[(size_t)(3 * k + row % 3) * N + row / 3] = s;
     }
 }
 

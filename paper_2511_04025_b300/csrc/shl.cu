@@ -7,9 +7,11 @@
 #include "pcg.cuh"
 #include "adjoint.cuh"
 #include "mg.cuh"
+#include "vec.cuh"
 
 #include <atomic>
 #include <functional>
+#include <type_traits>
 
 using namespace shl;
 
@@ -58,22 +60,38 @@ inline void raise_smem_limit(const void *fn, size_t bytes) {
         cudaGetLastError();
 }
 
-// z-extent of a CTA's tile: long enough to amortise the halo plane, short
-// enough to give two CTAs per SM at the grid sizes in use.
-inline int pick_tz(int r, int nvec) {
-    const size_t nxy = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * nvec;
-    int tz = 16;
-    while (tz > 4 && nxy * ((r + tz - 1) / tz) < 2 * 148) tz >>= 1;
-    return tz;
+// Number of z chunks of the apply grid.  Chunk heights differ by at most one
+// plane; the count minimises the modelled makespan
+//   ceil(CTAs / resident CTA slots) x (tallest chunk + 1 halo plane + 1 for the prologue),
+// i.e. it keeps whole waves of equal-work CTAs on the 148 SMs.
+inline int pick_zc(int r, int nvec, int ctas_per_sm) {
+    const long long nxy = (long long)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * nvec;
+    const long long slots = 148LL * ctas_per_sm;
+    int best = 1;
+    long long best_cost = -1;
+    for (int zc = 1; zc <= r && zc <= 128; ++zc) {
+        const long long h = (r + zc - 1) / zc;
+        const long long cost = ((nxy * zc + slots - 1) / slots) * (h + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best = zc;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+template <typename T>
+inline int apply_zc(int r, int nvec) {
+    return pick_zc(r, nvec, sizeof(T) == 4 ? 2 : 1);
 }
 
 template <typename T>
 int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
     using S = ApplyShape<T, kTX, kTY>;
     apply_smem_attr<T>();
-    a.tz = pick_tz(a.r, a.nvec);
+    a.zc = apply_zc<T>(a.r, a.nvec);
     const int tiles = ((a.r + kTX - 1) / kTX) * ((a.r + kTY - 1) / kTY);
-    const dim3 g(tiles, (a.r + a.tz - 1) / a.tz, a.nvec);
+    const dim3 g(tiles, a.zc, a.nvec);
     a.vec_ok = (a.r % S::VEC == 0) && ((reinterpret_cast<uintptr_t>(a.p) & 15) == 0);
     if (a.dot) {
         if (!a.partial) {
@@ -96,10 +114,26 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
     return SHL_OK;
 }
 
+// Transformed element operator for (nu, r), built on the host once and kept
+// in a small process-wide cache (building it costs tens of microseconds, more
+// than an apply launch at small grids).
 template <typename T>
 int get_op(shl_ctx *ctx, double nu, int r, ElemOp<T> *op) {
+    static std::mutex mu;
+    static std::map<std::pair<double, int>, ElemOp<T>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({nu, r});
+        if (it != cache.end()) {
+            *op = it->second;
+            return SHL_OK;
+        }
+    }
     const double off = build_elem_op<T>(nu, r, op);
     if (!(off < 1e-12)) return set_err(ctx, SHL_EINVAL, "element operator is not block diagonal (%g)", off);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() >= 64) cache.clear();
+    cache[{nu, r}] = *op;
     return SHL_OK;
 }
 
@@ -344,6 +378,56 @@ inline int replay(shl_ctx *ctx, cudaStream_t s, IterGraph *g, int times) {
 // Runs PCG from the residual in b.r and the iterate in b.x for the load cases
 // in want.  The device deactivates each case at convergence or st->maxit; the
 // host polls the active count every chunk of iterations.
+// Vector-kernel launches (vec.cuh): 16-byte chunks when the plane length
+// allows, scalar otherwise.
+template <typename T>
+inline void launch_vec_update(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom &g, const FineJacobi &fj, bool mg,
+                              const ApplyDot &ad, cudaStream_t s) {
+    constexpr int VW = (int)(16 / sizeof(T));
+    pcg_alpha_kernel<<<1, kVecThreads, 0, s>>>(va.st, ad);
+    ++ctx->launches;
+    if constexpr (std::is_same<T, float>::value) {
+        if (mg) {
+            if (g.V == VW)
+                vec_update_kernel<T, VW, true><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+            else
+                vec_update_kernel<T, 1, true><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+            ++ctx->launches;
+            return;
+        }
+    }
+    if (g.V == VW)
+        vec_update_kernel<T, VW, false><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+    else
+        vec_update_kernel<T, 1, false><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+    ++ctx->launches;
+}
+
+// Apply grid CTAs per load case (the deferred p.q partials of one case).
+template <typename T>
+inline int apply_ctas_per_case(int r) {
+    return ((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<T>(r, 6);
+}
+
+template <typename T>
+inline void launch_vec_direction(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom &g, cudaStream_t s) {
+    constexpr int VW = (int)(16 / sizeof(T));
+    if (g.V == VW)
+        vec_direction_kernel<T, VW><<<g.blocks(), kVecThreads, 0, s>>>(va, g);
+    else
+        vec_direction_kernel<T, 1><<<g.blocks(), kVecThreads, 0, s>>>(va, g);
+    ++ctx->launches;
+}
+
+inline void launch_vec_jacobi_rz(shl_ctx *ctx, const VecArgs<float> &va, const VecGeom &g, const FineJacobi &fj,
+                                 const float *t, cudaStream_t s) {
+    if (g.V == 4)
+        vec_jacobi_rz_kernel<4><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj, t);
+    else
+        vec_jacobi_rz_kernel<1><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj, t);
+    ++ctx->launches;
+}
+
 template <typename T>
 int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T> &b, PcgState *st, int want,
             int set_bnorm, cudaStream_t s, int *host_nactive, int max_iters_backstop) {
@@ -360,22 +444,22 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     a.q = b.q;
     a.pin = 1;
     a.dot = 1;
+    a.defer = 1;  // p.q is reduced by the update kernel
     a.st = st;
     a.ticket = &st->ticket_apply;
     const int chunk = 32;
     {
-        const int tz = pick_tz(r, 6);
-        const size_t nblk = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * ((r + tz - 1) / tz) * 6;
+        const size_t nblk = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<T>(r, 6) * 6;
         double *ap = nullptr;
         SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
         a.partial = ap;
     }
+    const VecGeom vg = vec_geom<T>((size_t)r * r * r);
     IterGraph graph;
     SHL_TRY(capture_iteration(ctx, s, &graph, [&]() -> int {
         SHL_TRY(launch_apply<T>(ctx, a, s));
-        pcg_update_kernel<T><<<gv, kBlk, 0, s>>>(va);
-        pcg_direction_kernel<T><<<gv, kBlk, 0, s>>>(va);
-        ctx->launches += 2;
+        launch_vec_update<T>(ctx, va, vg, FineJacobi{}, false, ApplyDot{a.partial, apply_ctas_per_case<T>(r)}, s);
+        launch_vec_direction<T>(ctx, va, vg, s);
         return SHL_OK;
     }));
     // the device deactivates every load case by st->maxit; the host cap is a backstop
@@ -547,7 +631,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     a.pin = 1;
                     SHL_TRY(launch_apply<float>(ctx, a, s));
                 } else {
-                    mg_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, x, nullptr, nullptr, 1.0f, 0, L.t,
+                    mg_stencil_kernel<<<grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s>>>(L.r, L.S, x, nullptr, nullptr, 1.0f, 0, L.t,
                                                                   nullptr);
                 }
                 const int g = grid1d(L.N, kBlk, 148 * 8);
@@ -581,7 +665,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             if (I == 0 || J == 0) continue;
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j)
-                    A[(3 * (I - 1) + i) * (size_t)m + 3 * (J - 1) + j] += Sh[(size_t)(dl * 9 + 3 * i + j) * C.N + I];
+                    A[(3 * (I - 1) + i) * (size_t)m + 3 * (J - 1) + j] += Sh[(I * 27 + dl) * 9 + 3 * i + j];
         }
     }
     // symmetrise (FP32 stencil rounding), Cholesky, explicit inverse
@@ -625,8 +709,13 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
 // z = V-cycle(b) for the pinned fine system; `fine` carries the density and
 // operator of the matrix-free apply.  Coarse levels use the fused stencil
 // kernel (residual, or a full Jacobi sweep into the other ping-pong buffer).
+// Fusion flags of the fine level: the first pre-smoothing step (x0 = w D^-1 b0)
+// was done by the caller; the last post-smoothing step is left to the caller
+// (on return lv[0].t = K x0 of the current x0).
+constexpr int kVcFirstFused = 1, kVcLastExternal = 2;
+
 inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const float *b0, float *x0, PcgState *st,
-                     cudaStream_t s) {
+                     cudaStream_t s, int fuse = 0) {
     auto fine_apply = [&](const float *x, float *t) -> int {
         ApplyArgs<float> a = fine;
         a.p = x;
@@ -639,7 +728,8 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     };
     auto sweep = [&](MgLevel &L, int mode) {  // coarse level: mode 1 residual into t, mode 2 Jacobi sweep
         float *out = mode == 1 ? L.t : (L.x == L.xa ? L.xb : L.xa);
-        mg_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, L.S, L.x, L.b, L.Dinv, L.omega, mode, out, st);
+        mg_stencil_kernel<<<grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s>>>(L.r, L.S, L.x, L.b, L.Dinv, L.omega, mode, out,
+                                                                       st);
         ++ctx->launches;
         if (mode == 2) L.x = out;
     };
@@ -649,8 +739,10 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     for (int l = 0; l < mg->L; ++l) {  // down: pre-smooth, restrict the residual
         MgLevel &L = mg->lv[l];
         const int g = grid1d(L.N);
-        mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
-        ++ctx->launches;
+        if (!(l == 0 && (fuse & kVcFirstFused))) {
+            mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
+            ++ctx->launches;
+        }
         if (l == 0) {
             for (int it = 1; it < mg->nu; ++it) {
                 SHL_TRY(fine_apply(L.x, L.t));
@@ -658,28 +750,32 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
                 ++ctx->launches;
             }
             SHL_TRY(fine_apply(L.x, L.t));
-            mg_restrict_kernel<<<grid1d(mg->lv[1].N), kBlk, 0, s>>>(mg->lv[1].r, L.b, L.t, mg->lv[1].b, st);
+            mg_restrict_kernel<<<dim3(grid1d(mg->lv[1].N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[1].r, L.b, L.t,
+                                                                                 mg->lv[1].b, st);
         } else {
             for (int it = 1; it < mg->nu; ++it) sweep(L, 2);
             sweep(L, 1);
-            mg_restrict_kernel<<<grid1d(mg->lv[l + 1].N), kBlk, 0, s>>>(mg->lv[l + 1].r, L.t, nullptr,
+            mg_restrict_kernel<<<dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[l + 1].r, L.t, nullptr,
                                                                          mg->lv[l + 1].b, st);
         }
         ++ctx->launches;
     }
     {
         MgLevel &C = mg->lv[mg->L];
-        mg_dense_solve_kernel<<<grid1d((size_t)6 * mg->n3, 128), 128, 0, s>>>(mg->n3, mg->Ainv, C.b, C.x, st);
+        mg_dense_solve_kernel<<<grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4), kBlk, 0, s>>>(mg->n3, mg->Ainv, C.b, C.x,
+                                                                                          st);
         ++ctx->launches;
     }
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
         MgLevel &L = mg->lv[l];
         const int g = grid1d(L.N);
-        mg_prolong_kernel<<<g, kBlk, 0, s>>>(mg->lv[l + 1].r, mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
+        mg_prolong_kernel<<<dim3(grid1d(L.N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[l + 1].r, mg->lv[l + 1].x, L.x,
+                                                                            l == 0 ? 1 : 0, st);
         ++ctx->launches;
         for (int it = 0; it < mg->nu; ++it) {
             if (l == 0) {
                 SHL_TRY(fine_apply(L.x, L.t));
+                if (it == mg->nu - 1 && (fuse & kVcLastExternal)) break;
                 mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
                 ++ctx->launches;
             } else {
@@ -805,28 +901,33 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             a.q = b.q;
             a.pin = 1;
             a.dot = 1;
+            a.defer = 1;  // p.q is reduced by the update kernel
             a.st = st;
             a.ticket = &st->ticket_apply;
             const int chunk = use_mg ? 8 : 32;
             // workspaces the iteration uses must exist before capture
             {
-                const int tz = pick_tz(r, 6);
-                const size_t nblk = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * ((r + tz - 1) / tz) * 6;
+                const size_t nblk =
+                    (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<float>(r, 6) * 6;
                 double *ap = nullptr;
                 SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
                 a.partial = ap;
             }
+            // one iteration: q = K p (+ p.q -> alpha); x, r update (+ r.r, and
+            // the first fine pre-smoothing step z = w D^-1 r); V-cycle; last
+            // fine post-smoothing step (+ r.z -> beta); p = z + beta p
+            const VecGeom vg = vec_geom<float>(N);
+            FineJacobi fj{};
+            if (use_mg) fj = FineJacobi{mg.lv[0].Dinv, mg.lv[0].omega, z32};
             auto iteration = [&]() -> int {
                 SHL_TRY(launch_apply<float>(ctx, a, s));
-                pcg_update_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                ++ctx->launches;
+                launch_vec_update<float>(ctx, va, vg, fj, use_mg, ApplyDot{a.partial, apply_ctas_per_case<float>(r)},
+                                         s);
                 if (use_mg) {
-                    SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s));
-                    pcg_rz_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                    ++ctx->launches;
+                    SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s, kVcFirstFused | kVcLastExternal));
+                    launch_vec_jacobi_rz(ctx, va, vg, fj, mg.lv[0].t, s);
                 }
-                pcg_direction_kernel<float><<<gv, kBlk, 0, s>>>(va);
-                ++ctx->launches;
+                launch_vec_direction<float>(ctx, va, vg, s);
                 return SHL_OK;
             };
             IterGraph graph;

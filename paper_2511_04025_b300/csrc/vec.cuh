@@ -1,0 +1,400 @@
+// vec.cuh -- the per-iteration vector kernels of the batched PCG (Sec. 4.2.2:
+// six load cases in the same kernels, per-case convergence and skip), laid
+// out for bandwidth: every block works on one load case k (its three planes)
+// and a strided range of 16-byte chunks (float4 / double2) of those planes,
+// so loads are vectorised and coalesced and the case's scalars are uniform
+// in the block.  The grid is 6 x bpk blocks, capped so that all of it is
+// resident at once (one wave, no tail).
+//
+// Fused multigrid smoothing (fine level, 3x3 block-Jacobi D^-1 stored [9][N]):
+//   vec_update  (MG mode) also writes the first pre-smoothing step z = w D^-1 r;
+//   vec_jacobi_rz  does the last post-smoothing step z += w D^-1 (r - t) and
+//                  the r.z product that gives beta.
+// Reductions are deterministic: per-block partials, combined by the last
+// block in a fixed order.
+#pragma once
+
+#include "apply.cuh"
+
+namespace shl {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocksPerSM = 4;  // register budget 64 per thread: one wave of 6 x bpk blocks
+
+// Launch shape of the vector kernels for n nodes.
+struct VecGeom {
+    int V = 1;          // elements per chunk (16 bytes, or 1 for ragged sizes)
+    size_t chunks = 0;  // chunks per plane
+    int bpk = 1;        // blocks per load case
+    int blocks() const { return 6 * bpk; }
+};
+
+template <typename T>
+inline VecGeom vec_geom(size_t n) {
+    VecGeom g;
+    g.V = (n % (16 / sizeof(T)) == 0) ? (int)(16 / sizeof(T)) : 1;
+    g.chunks = n / g.V;
+    size_t b = (g.chunks + kVecThreads - 1) / kVecThreads;
+    const size_t cap = 148 * kVecBlocksPerSM / 6;  // the whole grid resident at once
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    g.bpk = (int)b;
+    return g;
+}
+
+template <typename T, int V>
+struct Chunk {
+    T v[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ Chunk<T, V> ldc(const T *p) {
+    Chunk<T, V> c;
+    if constexpr (V * sizeof(T) == 16) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p);
+            c.v[0] = t.x, c.v[1] = t.y, c.v[2] = t.z, c.v[3] = t.w;
+        } else {
+            const double2 t = *reinterpret_cast<const double2 *>(p);
+            c.v[0] = t.x, c.v[1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) c.v[e] = p[e];
+    }
+    return c;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stc(T *p, const Chunk<T, V> &c) {
+    if constexpr (V * sizeof(T) == 16) {
+        if constexpr (sizeof(T) == 4)
+            *reinterpret_cast<float4 *>(p) = make_float4(c.v[0], c.v[1], c.v[2], c.v[3]);
+        else
+            *reinterpret_cast<double2 *>(p) = make_double2(c.v[0], c.v[1]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) p[e] = c.v[e];
+    }
+}
+
+// Last block: tot[v * 6 + k] = sum over the bpk blocks of case k of
+// partial[(k * bpk + j) * 2 + v], in a fixed order.
+__device__ inline void sum_case_partials(const double *partial, int bpk, double (&tot)[12]) {
+    __shared__ double red[12][32];
+    double s[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) s[m] = 0.0;
+    for (int j = threadIdx.x; j < bpk; j += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            s[k] += __ldcg(partial + ((size_t)k * bpk + j) * 2 + 0);
+            s[6 + k] += __ldcg(partial + ((size_t)k * bpk + j) * 2 + 1);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+        double x = s[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[m][warp] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+        double x = 0.0;
+        for (int w = 0; w < nw; ++w) x += red[m][w];
+        tot[m] = x;
+    }
+}
+
+// Block partials (d0, d1) -> partial[blockIdx.x * 2 + {0, 1}].
+template <typename T>
+__device__ inline void store_block_pair(const DotAcc<T> &d0, const DotAcc<T> &d1, double *partial) {
+    double v[2] = {d0.get(), d1.get()};
+    block_reduce_store<2>(v, partial, blockIdx.x);
+}
+
+// v[off + k] for a run-time k < 6 without local-memory indexing.
+template <int NV>
+__device__ __forceinline__ double pick6(const double (&v)[NV], int off, int k) {
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        if (i == k) r = v[off + i];
+    return r;
+}
+
+// Per-CTA partial sums of p.q left by the stiffness apply (deferred mode):
+// partial[(k * per_case + b) * 6 + k] for the per_case CTAs of load case k.
+struct ApplyDot {
+    const double *partial;
+    int per_case;
+};
+
+// (p.q)_k of all six load cases at once (one pass over the partials, one
+// block reduction), the same values in every thread, fixed order.
+__device__ inline void case_pq_all(const ApplyDot &ad, double (&pq)[6]) {
+    __shared__ double red[6][32];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < ad.per_case; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += __ldcg(ad.partial + ((size_t)k * ad.per_case + b) * 6 + k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0) red[k][warp] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[k][w];
+        pq[k] = t;
+    }
+}
+
+// One block: alpha_k = rz_k / (p.q)_k for the active load cases, from the
+// stiffness apply's deferred per-CTA partials; a non-positive or non-finite
+// p.q stops the case with a numeric error.
+__global__ void pcg_alpha_kernel(PcgState *st, ApplyDot ad) {
+    if (st->nactive == 0) return;
+    double pq[6];
+    case_pq_all(ad, pq);
+    // lane k of warp 0 handles load case k (the state loads run in parallel)
+    if (threadIdx.x < 32) {
+        const int k = threadIdx.x;
+        int act = 0;
+        if (k < 6) {
+            act = st->active[k];
+            if (act) {
+                const double p = pick6(pq, 0, k);
+                if (!(p > 0.0) || !isfinite(p)) {
+                    st->numeric_err = 1;
+                    st->alpha[k] = 0.0;
+                    act = 0;
+                    st->active[k] = 0;
+                } else {
+                    st->alpha[k] = st->rz[k] / p;
+                }
+            }
+        }
+        const int na = __reduce_add_sync(0xffffffffu, act);
+        if (k == 0) st->nactive = na;
+    }
+}
+
+struct FineJacobi {
+    const float *Dinv;  // [9][N] 3x3 block inverses (row-major per node)
+    float omega;
+    float *z;           // output (update) / in-out (jacobi_rz), 18 planes
+};
+
+// x += alpha p ; r -= alpha q  (active cases, alpha from pcg_alpha_kernel), rr = r.r
+//   Jacobi mode (MG = false): rz = r . D^-1 r with the point-Jacobi diagonal
+//   a.dinv; the last block sets beta and rz.
+//   Multigrid mode: z = w D^-1 r (first pre-smoothing step); beta comes later
+//   from vec_jacobi_rz.
+// Last block: iteration count, convergence and budget tests, nactive.
+template <typename T, int V, bool MG>
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kernel(VecArgs<T> a, VecGeom g, FineJacobi fj) {
+    PcgState *st = a.st;
+    if (st->nactive == 0) return;  // uniform: the solve has finished
+    const int k = blockIdx.x / g.bpk, j = blockIdx.x - k * g.bpk;
+    const bool act = st->active[k] != 0;
+    DotAcc<T> drz, drr;
+    if (act) {
+        const T al = (T)st->alpha[k];
+        const size_t N = a.N;
+        T *__restrict__ x = a.x + (size_t)3 * k * N;
+        T *__restrict__ r = a.r + (size_t)3 * k * N;
+        const T *__restrict__ p = a.p + (size_t)3 * k * N;
+        const T *__restrict__ q = a.q + (size_t)3 * k * N;
+        for (size_t c = (size_t)j * kVecThreads + threadIdx.x; c < g.chunks; c += (size_t)g.bpk * kVecThreads) {
+            const size_t n0 = c * V;
+            Chunk<T, V> rn[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)i * N + n0;
+                Chunk<T, V> xv = ldc<T, V>(x + o), pv = ldc<T, V>(p + o), rv = ldc<T, V>(r + o),
+                            qv = ldc<T, V>(q + o);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    xv.v[e] += al * pv.v[e];
+                    rv.v[e] -= al * qv.v[e];
+                    drr.add(rv.v[e] * rv.v[e]);
+                }
+                stc<T, V>(x + o, xv);
+                stc<T, V>(r + o, rv);
+                rn[i] = rv;
+            }
+            if constexpr (MG) {
+                float D[9][V];
+#pragma unroll
+                for (int m = 0; m < 9; ++m) {
+                    const Chunk<float, V> dv = ldc<float, V>(fj.Dinv + (size_t)m * N + n0);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) D[m][e] = dv.v[e];
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    Chunk<float, V> zv;
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        zv.v[e] = fj.omega * (D[3 * i][e] * (float)rn[0].v[e] + D[3 * i + 1][e] * (float)rn[1].v[e] +
+                                              D[3 * i + 2][e] * (float)rn[2].v[e]);
+                    stc<float, V>(fj.z + (size_t)(3 * k + i) * N + n0, zv);
+                }
+            } else {
+                const Chunk<T, V> dv = ldc<T, V>(a.dinv + n0);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int e = 0; e < V; ++e) drz.add(rn[i].v[e] * (dv.v[e] * rn[i].v[e]));
+            }
+        }
+    }
+    store_block_pair<T>(drz, drr, a.partial);
+    if (!last_block_ticket(&st->ticket_update, gridDim.x)) return;
+    double tot[12];
+    sum_case_partials(a.partial, g.bpk, tot);
+    // lane kk of warp 0 handles load case kk (the state loads run in parallel)
+    if (threadIdx.x < 32) {
+        const int kk = threadIdx.x;
+        int act = 0;
+        if (kk < 6) {
+            act = st->active[kk];
+            if (act) {
+                const int it = st->iters[kk] + 1;
+                st->iters[kk] = it;
+                const double rz = pick6(tot, 0, kk), rr = pick6(tot, 6, kk);
+                st->rr[kk] = rr;
+                if (!isfinite(rz) || !isfinite(rr)) {
+                    st->numeric_err = 1;
+                    act = 0;
+                } else if (rr <= st->tol2 * st->bnorm2[kk]) {
+                    act = 0;
+                } else if (it >= st->maxit) {
+                    act = 0;
+                } else if (!MG) {
+                    st->beta[kk] = rz / st->rz[kk];
+                    st->rz[kk] = rz;
+                }
+                if (!act) st->active[kk] = 0;
+            }
+        }
+        const int na = __reduce_add_sync(0xffffffffu, act);
+        if (kk == 0) st->nactive = na;
+    }
+}
+
+// Multigrid mode, last post-smoothing step at the fine level and beta:
+// z += w D^-1 (r - t) (active cases; t = K z from the preceding apply), then
+// rz = r . z; last block: beta = rz / rz_prev, rz_prev = rz.
+template <int V>
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_jacobi_rz_kernel(VecArgs<float> a, VecGeom g, FineJacobi fj,
+                                                                    const float *__restrict__ t) {
+    PcgState *st = a.st;
+    if (st->nactive == 0) return;
+    const int k = blockIdx.x / g.bpk, j = blockIdx.x - k * g.bpk;
+    const bool act = st->active[k] != 0;
+    DotAcc<float> drz, dnone;
+    if (act) {
+        const size_t N = a.N;
+        const float *__restrict__ r = a.r + (size_t)3 * k * N;
+        const float *__restrict__ tk = t + (size_t)3 * k * N;
+        float *__restrict__ z = fj.z + (size_t)3 * k * N;
+        for (size_t c = (size_t)j * kVecThreads + threadIdx.x; c < g.chunks; c += (size_t)g.bpk * kVecThreads) {
+            const size_t n0 = c * V;
+            Chunk<float, V> rv[3], dv[3], zv[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)i * N + n0;
+                rv[i] = ldc<float, V>(r + o);
+                const Chunk<float, V> tv = ldc<float, V>(tk + o);
+                zv[i] = ldc<float, V>(z + o);
+#pragma unroll
+                for (int e = 0; e < V; ++e) dv[i].v[e] = rv[i].v[e] - tv.v[e];
+            }
+            float D[9][V];
+#pragma unroll
+            for (int m = 0; m < 9; ++m) {
+                const Chunk<float, V> d = ldc<float, V>(fj.Dinv + (size_t)m * N + n0);
+#pragma unroll
+                for (int e = 0; e < V; ++e) D[m][e] = d.v[e];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    zv[i].v[e] += fj.omega * (D[3 * i][e] * dv[0].v[e] + D[3 * i + 1][e] * dv[1].v[e] +
+                                              D[3 * i + 2][e] * dv[2].v[e]);
+                    drz.add(rv[i].v[e] * zv[i].v[e]);
+                }
+                stc<float, V>(z + (size_t)i * N + n0, zv[i]);
+            }
+        }
+    }
+    store_block_pair<float>(drz, dnone, a.partial);
+    if (!last_block_ticket(&st->ticket_aux, gridDim.x)) return;
+    double tot[12];
+    sum_case_partials(a.partial, g.bpk, tot);
+    if (threadIdx.x < 32) {
+        const int kk = threadIdx.x;
+        int act = 0;
+        if (kk < 6) {
+            act = st->active[kk];
+            if (act) {
+                const double rz = pick6(tot, 0, kk);
+                if (!isfinite(rz) || !(rz > 0.0)) {
+                    st->numeric_err = 1;
+                    act = 0;
+                    st->active[kk] = 0;
+                } else {
+                    st->beta[kk] = rz / st->rz[kk];
+                    st->rz[kk] = rz;
+                }
+            }
+        }
+        const int na = __reduce_add_sync(0xffffffffu, act);
+        if (kk == 0) st->nactive = na;
+    }
+}
+
+// p = z + beta p (multigrid) or p = D^-1 r + beta p (point Jacobi), active cases.
+template <typename T, int V>
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_direction_kernel(VecArgs<T> a, VecGeom g) {
+    PcgState *st = a.st;
+    if (st->nactive == 0) return;
+    const int k = blockIdx.x / g.bpk, j = blockIdx.x - k * g.bpk;
+    if (!st->active[k]) return;
+    const T be = (T)st->beta[k];
+    const size_t N = a.N;
+    T *__restrict__ p = a.p + (size_t)3 * k * N;
+    const T *__restrict__ r = a.r + (size_t)3 * k * N;
+    const T *__restrict__ z = a.z ? a.z + (size_t)3 * k * N : nullptr;
+    for (size_t c = (size_t)j * kVecThreads + threadIdx.x; c < g.chunks; c += (size_t)g.bpk * kVecThreads) {
+        const size_t n0 = c * V;
+        Chunk<T, V> di;
+        if (!z) di = ldc<T, V>(a.dinv + n0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t o = (size_t)i * N + n0;
+            Chunk<T, V> pv = ldc<T, V>(p + o);
+            if (z) {
+                const Chunk<T, V> zv = ldc<T, V>(z + o);
+#pragma unroll
+                for (int e = 0; e < V; ++e) pv.v[e] = zv.v[e] + be * pv.v[e];
+            } else {
+                const Chunk<T, V> rv = ldc<T, V>(r + o);
+#pragma unroll
+                for (int e = 0; e < V; ++e) pv.v[e] = di.v[e] * rv.v[e] + be * pv.v[e];
+            }
+            stc<T, V>(p + o, pv);
+        }
+    }
+}
+
+}  // namespace shl
