@@ -341,8 +341,10 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__r
 
 // bc = R (bf - tf): coarse node I gathers w(a) (bf - tf)[2I + a] over its 27
 // fine neighbours; tf may be null (bf is then the residual itself).  Grid:
-// x over coarse nodes (one per thread), y over the 18 planes; converged load
-// cases are skipped.
+// x over coarse nodes (one per thread), y over the 18 planes.  Each of the 9
+// fine rows is read as one 8-byte pair (2ix, 2ix + 1); the left neighbour
+// 2ix - 1 is the previous lane's right value when that lane holds ix - 1 of
+// the same row.  Converged load cases are skipped.
 __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *__restrict__ bf,
                                                           const float *__restrict__ tf, float *__restrict__ bc,
                                                           const PcgState *st) {
@@ -355,56 +357,84 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *_
     const size_t Nf = (size_t)rrf * rf;
     const float *bm = bf + (size_t)m * Nf;
     const float *tm = tf ? tf + (size_t)m * Nf : nullptr;
-    for (unsigned I = blockIdx.x * blockDim.x + threadIdx.x; I < Nc; I += gridDim.x * blockDim.x) {
-        const int ix = (int)(I % (unsigned)rc), iy = (int)((I / (unsigned)rc) % (unsigned)rc),
-                  iz = (int)(I / ((unsigned)rc * rc));
+    const int lane = threadIdx.x & 31;
+    // every lane runs the same number of iterations (the shuffles need the whole warp)
+    const unsigned stride = gridDim.x * blockDim.x;
+    const unsigned iters = (Nc + stride - 1) / stride;
+    for (unsigned it = 0; it < iters; ++it) {
+        const unsigned I = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool valid = I < Nc;
+        const unsigned Iv = valid ? I : 0;
+        const int ix = (int)(Iv % (unsigned)rc), iy = (int)((Iv / (unsigned)rc) % (unsigned)rc),
+                  iz = (int)(Iv / ((unsigned)rc * rc));
         const unsigned zo[3] = {(unsigned)wrap_l(2 * iz - 1, rf) * rrf, (unsigned)(2 * iz) * rrf,
                                 (unsigned)wrap_l(2 * iz + 1, rf) * rrf};
         const unsigned yo[3] = {(unsigned)wrap_l(2 * iy - 1, rf) * rf, (unsigned)(2 * iy) * rf,
                                 (unsigned)wrap_l(2 * iy + 1, rf) * rf};
-        const unsigned xo[3] = {(unsigned)wrap_l(2 * ix - 1, rf), (unsigned)(2 * ix), (unsigned)wrap_l(2 * ix + 1, rf)};
+        const bool left_in_warp = lane > 0 && ix > 0;
         float acc = 0.0f;
 #pragma unroll
         for (int az = 0; az < 3; ++az)
 #pragma unroll
             for (int ay = 0; ay < 3; ++ay) {
-                float row = 0.0f;
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    const unsigned f = zo[az] + yo[ay] + xo[ax];
-                    const float v = tm ? bm[f] - tm[f] : bm[f];
-                    row += (ax == 1 ? 1.0f : 0.5f) * v;
+                const unsigned row = zo[az] + yo[ay];
+                float2 c = *reinterpret_cast<const float2 *>(bm + row + 2 * ix);
+                if (tm) {
+                    const float2 t = *reinterpret_cast<const float2 *>(tm + row + 2 * ix);
+                    c.x -= t.x;
+                    c.y -= t.y;
                 }
-                acc += (az == 1 ? 1.0f : 0.5f) * (ay == 1 ? 1.0f : 0.5f) * row;
+                float left = __shfl_up_sync(0xffffffffu, c.y, 1);
+                if (!left_in_warp) {
+                    const unsigned xl = (unsigned)wrap_l(2 * ix - 1, rf);
+                    left = tm ? bm[row + xl] - tm[row + xl] : bm[row + xl];
+                }
+                const float rowsum = c.x + 0.5f * (left + c.y);
+                acc += (az == 1 ? 1.0f : 0.5f) * (ay == 1 ? 1.0f : 0.5f) * rowsum;
             }
-        bc[(size_t)m * Nc + I] = acc;
+        if (valid) bc[(size_t)m * Nc + I] = acc;
     }
 }
 
-// xf += P xc (trilinear): fine node i takes the coarse nodes around it
-// (odd coordinates average their two coarse neighbours).  Grid: x over fine
-// nodes, y over the 18 planes; converged load cases are skipped; with pin0
-// the fine node 0 (pinned) is left unchanged.
+// xf += P xc (trilinear).  One thread per (plane m = grid y, coarse node C):
+// it loads the 8 coarse values of the cell [C, C + 1]^3 once and updates the
+// 8 fine nodes 2C + (a, b, c), a, b, c in {0, 1} (odd fine coordinates average
+// their two coarse neighbours), two x-neighbours per 8-byte access.
+// Converged load cases are skipped; with pin0 the fine node 0 (pinned) is
+// left unchanged.
 __global__ void __launch_bounds__(256) mg_prolong_kernel(int rc, const float *__restrict__ xc,
                                                          float *__restrict__ xf, int pin0, const PcgState *st) {
     if (mg_done(st)) return;
     const int m = blockIdx.y;
     if (st && !st->active[m / 3]) return;
     const int rf = 2 * rc;
-    const unsigned Nf = (unsigned)rf * rf * rf, rrc = (unsigned)rc * rc;
-    const float *xm = xc + (size_t)m * rrc * rc;
-    float *xo = xf + (size_t)m * Nf;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < Nf; i += gridDim.x * blockDim.x) {
-        if (pin0 && i == 0) continue;
-        const int fx = (int)(i % (unsigned)rf), fy = (int)((i / (unsigned)rf) % (unsigned)rf),
-                  fz = (int)(i / ((unsigned)rf * rf));
-        const int cx0 = fx >> 1, cy0 = fy >> 1, cz0 = fz >> 1;
-        const unsigned cx1 = (fx & 1) ? wrap_l(cx0 + 1, rc) : cx0;
-        const unsigned y0 = (unsigned)cy0 * rc, y1 = (unsigned)((fy & 1) ? wrap_l(cy0 + 1, rc) : cy0) * rc;
-        const unsigned z0 = (unsigned)cz0 * rrc, z1 = (unsigned)((fz & 1) ? wrap_l(cz0 + 1, rc) : cz0) * rrc;
-        const float v = xm[z0 + y0 + cx0] + xm[z0 + y0 + cx1] + xm[z0 + y1 + cx0] + xm[z0 + y1 + cx1] +
-                        xm[z1 + y0 + cx0] + xm[z1 + y0 + cx1] + xm[z1 + y1 + cx0] + xm[z1 + y1 + cx1];
-        xo[i] += 0.125f * v;
+    const unsigned rrc = (unsigned)rc * rc, Nc = rrc * rc, rrf = (unsigned)rf * rf;
+    const float *xm = xc + (size_t)m * Nc;
+    float *xo = xf + (size_t)m * rrf * rf;
+    for (unsigned I = blockIdx.x * blockDim.x + threadIdx.x; I < Nc; I += gridDim.x * blockDim.x) {
+        const int cx = (int)(I % (unsigned)rc), cy = (int)((I / (unsigned)rc) % (unsigned)rc), cz = (int)(I / rrc);
+        const unsigned x1 = (unsigned)wrap_l(cx + 1, rc), y0 = (unsigned)cy * rc, y1 = (unsigned)wrap_l(cy + 1, rc) * rc,
+                       z0 = (unsigned)cz * rrc, z1 = (unsigned)wrap_l(cz + 1, rc) * rrc;
+        float e[2][2][2];  // [c][b][x]: the cell's values combined along z and y
+#pragma unroll
+        for (int xi = 0; xi < 2; ++xi) {
+            const unsigned xx = xi ? x1 : (unsigned)cx;
+            const float v00 = xm[z0 + y0 + xx], v01 = xm[z0 + y1 + xx], v10 = xm[z1 + y0 + xx], v11 = xm[z1 + y1 + xx];
+            e[0][0][xi] = v00;
+            e[0][1][xi] = 0.5f * (v00 + v01);
+            e[1][0][xi] = 0.5f * (v00 + v10);
+            e[1][1][xi] = 0.25f * ((v00 + v01) + (v10 + v11));
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                float2 *f = reinterpret_cast<float2 *>(xo + ((size_t)(2 * cz + c) * rf + (2 * cy + b)) * rf + 2 * cx);
+                float2 v = *f;
+                if (!(pin0 && I == 0 && c == 0 && b == 0)) v.x += e[c][b][0];
+                v.y += 0.5f * (e[c][b][0] + e[c][b][1]);
+                *f = v;
+            }
     }
 }
 

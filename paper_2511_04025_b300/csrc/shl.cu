@@ -769,8 +769,9 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
         MgLevel &L = mg->lv[l];
         const int g = grid1d(L.N);
-        mg_prolong_kernel<<<dim3(grid1d(L.N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[l + 1].r, mg->lv[l + 1].x, L.x,
-                                                                            l == 0 ? 1 : 0, st);
+        mg_prolong_kernel<<<dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[l + 1].r,
+                                                                                        mg->lv[l + 1].x, L.x,
+                                                                                        l == 0 ? 1 : 0, st);
         ++ctx->launches;
         for (int it = 0; it < mg->nu; ++it) {
             if (l == 0) {
