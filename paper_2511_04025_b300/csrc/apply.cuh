@@ -57,6 +57,7 @@ struct ApplyArgs {
     double *dot_out;       // 6 sums (may be null)
     PcgState *st;          // PCG mode: active flags in, alpha = rz / pq out
     const int *active_in;  // per load-case flags when st == null (may be null)
+    int case_mask;         // bit k: load case k is computed (others: output and dot left untouched)
     int vec_ok;            // p is 16-byte aligned and r is a multiple of 16 / sizeof(T)
     ElemOp<T> op;
 };
@@ -103,6 +104,7 @@ __host__ __device__ inline int wrap_near(int v, int r) { return v < 0 ? v + r : 
 template <typename T, int TX, int TY, bool RESID>
 __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4 ? 2 : 1)
     apply_kernel(const ApplyArgs<T> a) {
+    pdl_enter();
     using S = ApplyShape<T, TX, TY>;
     constexpr int EX = S::EX, NT = S::NT, PITCH = S::PITCH, NY = S::NY, PLANE = S::PLANE, OFF = S::OFF,
                   VEC = S::VEC;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
     bool act = k < a.nvec;
     if (act && a.st) act = a.st->active[k] != 0;
     if (act && a.active_in) act = a.active_in[k] != 0;
+    act = act && ((a.case_mask >> k) & 1);
     DotAcc<T> dacc;
 
     if (act) {
@@ -358,7 +361,8 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
     sum_partials_ordered<6>(a.partial, nblocks, tot);
     if (threadIdx.x == 0) {
         if (a.dot_out)
-            for (int kk = 0; kk < 6; ++kk) a.dot_out[kk] = tot[kk];
+            for (int kk = 0; kk < 6; ++kk)
+                if ((a.case_mask >> kk) & 1) a.dot_out[kk] = tot[kk];
         if (a.st) {
             for (int kk = 0; kk < 6; ++kk) {
                 if (!a.st->active[kk]) continue;

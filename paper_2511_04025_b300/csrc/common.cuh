@@ -150,6 +150,21 @@ __host__ __device__ inline int wrapi(int v, int r) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Kernels of the PCG iteration start with
+// pdl_wait() (nothing of the preceding kernel is read or overwritten before
+// it has completed and its memory is visible) and then pdl_trigger() (the
+// next kernel may be launched once every CTA of this one has started), so the
+// next launch overlaps this kernel's tail instead of following it.  Both are
+// no-ops for an ordinary launch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic grid reductions: every block writes its partial sums to
 // partial[block*NV + v]; the last block to finish (ticket counter) combines
 // the partials in a fixed order.  Bitwise reproducible for a fixed launch

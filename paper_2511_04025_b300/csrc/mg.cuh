@@ -195,6 +195,7 @@ __global__ void mg_dinv_fine_kernel(int r, const uint8_t *mask, const double *rh
 __global__ void mg_jacobi_kernel(size_t N, const float *__restrict__ b, const float *__restrict__ t,
                                  const float *__restrict__ Dinv, float w, float *__restrict__ x, int first,
                                  const PcgState *st) {
+    pdl_enter();
     if (mg_done(st)) return;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         float D[9];
@@ -276,6 +277,7 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__r
                                                          const float *__restrict__ x, const float *__restrict__ b,
                                                          const float *__restrict__ Dinv, float w, int mode,
                                                          float *__restrict__ out, const PcgState *st) {
+    pdl_enter();
     if (mg_done(st)) return;
     const unsigned N = (unsigned)r * r * r;
     const int lane = threadIdx.x & 31;
@@ -348,6 +350,7 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__r
 __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *__restrict__ bf,
                                                           const float *__restrict__ tf, float *__restrict__ bc,
                                                           const PcgState *st) {
+    pdl_enter();
     if (mg_done(st)) return;
     const int m = blockIdx.y;
     if (st && !st->active[m / 3]) return;
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *_
 // left unchanged.
 __global__ void __launch_bounds__(256) mg_prolong_kernel(int rc, const float *__restrict__ xc,
                                                          float *__restrict__ xf, int pin0, const PcgState *st) {
+    pdl_enter();
     if (mg_done(st)) return;
     const int m = blockIdx.y;
     if (st && !st->active[m / 3]) return;
@@ -489,6 +493,7 @@ __global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nr
 // Ainv), fixed shuffle tree.
 __global__ void mg_dense_solve_kernel(int n3, const float *__restrict__ Ainv, const float *__restrict__ b,
                                       float *__restrict__ x, const PcgState *st) {
+    pdl_enter();
     if (mg_done(st)) return;
     const int N = n3 / 3;
     const int lane = threadIdx.x & 31;

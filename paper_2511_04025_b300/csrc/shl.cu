@@ -12,6 +12,7 @@
 #include <atomic>
 #include <functional>
 #include <type_traits>
+#include <utility>
 
 using namespace shl;
 
@@ -60,6 +61,25 @@ inline void raise_smem_limit(const void *fn, size_t bytes) {
         cudaGetLastError();
 }
 
+// Launch with programmatic stream serialisation (the kernel starts with
+// pdl_enter(): it waits for the preceding kernel before touching memory, and
+// its launch overlaps that kernel's tail).
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Number of z chunks of the apply grid.  Chunk heights differ by at most one
 // plane; the count minimises the modelled makespan
 //   ceil(CTAs / resident CTA slots) x (tallest chunk + 1 halo plane + 1 for the prologue),
@@ -106,9 +126,9 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
         }
     }
     if (a.resid)
-        apply_kernel<T, kTX, kTY, true><<<g, S::THREADS, S::smem(), s>>>(a);
+        pdl_launch(apply_kernel<T, kTX, kTY, true>, g, S::THREADS, S::smem(), s, a);
     else
-        apply_kernel<T, kTX, kTY, false><<<g, S::THREADS, S::smem(), s>>>(a);
+        pdl_launch(apply_kernel<T, kTX, kTY, false>, g, S::THREADS, S::smem(), s, a);
     ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
@@ -309,6 +329,7 @@ ApplyArgs<T> make_apply(int r, const Density &den, const ElemOp<T> &op) {
     a.r = r;
     a.N = (size_t)r * r * r;
     a.nvec = 6;
+    a.case_mask = 0x3f;
     a.mask = den.mask;
     a.rho = den.rho;
     a.E = (T)den.E;
@@ -384,22 +405,22 @@ template <typename T>
 inline void launch_vec_update(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom &g, const FineJacobi &fj, bool mg,
                               const ApplyDot &ad, cudaStream_t s) {
     constexpr int VW = (int)(16 / sizeof(T));
-    pcg_alpha_kernel<<<1, kVecThreads, 0, s>>>(va.st, ad);
+    pdl_launch(pcg_alpha_kernel, 1, kVecThreads, 0, s, va.st, ad);
     ++ctx->launches;
     if constexpr (std::is_same<T, float>::value) {
         if (mg) {
             if (g.V == VW)
-                vec_update_kernel<T, VW, true><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+                pdl_launch(vec_update_kernel<T, VW, true>, g.blocks(), kVecThreads, 0, s, va, g, fj);
             else
-                vec_update_kernel<T, 1, true><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+                pdl_launch(vec_update_kernel<T, 1, true>, g.blocks(), kVecThreads, 0, s, va, g, fj);
             ++ctx->launches;
             return;
         }
     }
     if (g.V == VW)
-        vec_update_kernel<T, VW, false><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+        pdl_launch(vec_update_kernel<T, VW, false>, g.blocks(), kVecThreads, 0, s, va, g, fj);
     else
-        vec_update_kernel<T, 1, false><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj);
+        pdl_launch(vec_update_kernel<T, 1, false>, g.blocks(), kVecThreads, 0, s, va, g, fj);
     ++ctx->launches;
 }
 
@@ -413,18 +434,18 @@ template <typename T>
 inline void launch_vec_direction(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom &g, cudaStream_t s) {
     constexpr int VW = (int)(16 / sizeof(T));
     if (g.V == VW)
-        vec_direction_kernel<T, VW><<<g.blocks(), kVecThreads, 0, s>>>(va, g);
+        pdl_launch(vec_direction_kernel<T, VW>, g.blocks(), kVecThreads, 0, s, va, g);
     else
-        vec_direction_kernel<T, 1><<<g.blocks(), kVecThreads, 0, s>>>(va, g);
+        pdl_launch(vec_direction_kernel<T, 1>, g.blocks(), kVecThreads, 0, s, va, g);
     ++ctx->launches;
 }
 
 inline void launch_vec_jacobi_rz(shl_ctx *ctx, const VecArgs<float> &va, const VecGeom &g, const FineJacobi &fj,
                                  const float *t, cudaStream_t s) {
     if (g.V == 4)
-        vec_jacobi_rz_kernel<4><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj, t);
+        pdl_launch(vec_jacobi_rz_kernel<4>, g.blocks(), kVecThreads, 0, s, va, g, fj, t);
     else
-        vec_jacobi_rz_kernel<1><<<g.blocks(), kVecThreads, 0, s>>>(va, g, fj, t);
+        pdl_launch(vec_jacobi_rz_kernel<1>, g.blocks(), kVecThreads, 0, s, va, g, fj, t);
     ++ctx->launches;
 }
 
@@ -484,9 +505,12 @@ struct SolveOut {
 
 // Residual f - K x (FP64) with its squared norms per load case; pin selects
 // the pinned system; x == nullptr means x = 0 (the loads f themselves).
+// out = f - K x (pinned), FP64, for the load cases in mask (others untouched),
+// and |out|^2 per computed case into dot_out.
 inline int resid64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double> &op, const double *x, double *out,
-                   int pin, double *dot_out, cudaStream_t s) {
+                   int pin, double *dot_out, cudaStream_t s, int mask = 0x3f) {
     ApplyArgs<double> a = make_apply<double>(r, den, op);
+    a.case_mask = mask;
     a.p = x;
     a.q = out;
     a.pin = pin;
@@ -631,8 +655,8 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     a.pin = 1;
                     SHL_TRY(launch_apply<float>(ctx, a, s));
                 } else {
-                    mg_stencil_kernel<<<grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s>>>(L.r, L.S, x, nullptr, nullptr, 1.0f, 0, L.t,
-                                                                  nullptr);
+                    pdl_launch(mg_stencil_kernel, grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s, L.r, L.S, x, nullptr,
+                               nullptr, 1.0f, 0, L.t, nullptr);
                 }
                 const int g = grid1d(L.N, kBlk, 148 * 8);
                 mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + it);
@@ -728,8 +752,8 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     };
     auto sweep = [&](MgLevel &L, int mode) {  // coarse level: mode 1 residual into t, mode 2 Jacobi sweep
         float *out = mode == 1 ? L.t : (L.x == L.xa ? L.xb : L.xa);
-        mg_stencil_kernel<<<grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s>>>(L.r, L.S, L.x, L.b, L.Dinv, L.omega, mode, out,
-                                                                       st);
+        pdl_launch(mg_stencil_kernel, grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s, L.r, L.S, L.x, L.b, L.Dinv,
+                   L.omega, mode, out, st);
         ++ctx->launches;
         if (mode == 2) L.x = out;
     };
@@ -740,44 +764,43 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
         MgLevel &L = mg->lv[l];
         const int g = grid1d(L.N);
         if (!(l == 0 && (fuse & kVcFirstFused))) {
-            mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
+            pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
             ++ctx->launches;
         }
         if (l == 0) {
             for (int it = 1; it < mg->nu; ++it) {
                 SHL_TRY(fine_apply(L.x, L.t));
-                mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
+                pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
                 ++ctx->launches;
             }
             SHL_TRY(fine_apply(L.x, L.t));
-            mg_restrict_kernel<<<dim3(grid1d(mg->lv[1].N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[1].r, L.b, L.t,
-                                                                                 mg->lv[1].b, st);
+            pdl_launch(mg_restrict_kernel, dim3(grid1d(mg->lv[1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[1].r, L.b,
+                       L.t, mg->lv[1].b, st);
         } else {
             for (int it = 1; it < mg->nu; ++it) sweep(L, 2);
             sweep(L, 1);
-            mg_restrict_kernel<<<dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[l + 1].r, L.t, nullptr,
-                                                                         mg->lv[l + 1].b, st);
+            pdl_launch(mg_restrict_kernel, dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[l + 1].r,
+                       L.t, nullptr, mg->lv[l + 1].b, st);
         }
         ++ctx->launches;
     }
     {
         MgLevel &C = mg->lv[mg->L];
-        mg_dense_solve_kernel<<<grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4), kBlk, 0, s>>>(mg->n3, mg->Ainv, C.b, C.x,
-                                                                                          st);
+        pdl_launch(mg_dense_solve_kernel, grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4), kBlk, 0, s, mg->n3,
+                   mg->Ainv, C.b, C.x, st);
         ++ctx->launches;
     }
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
         MgLevel &L = mg->lv[l];
         const int g = grid1d(L.N);
-        mg_prolong_kernel<<<dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s>>>(mg->lv[l + 1].r,
-                                                                                        mg->lv[l + 1].x, L.x,
-                                                                                        l == 0 ? 1 : 0, st);
+        pdl_launch(mg_prolong_kernel, dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[l + 1].r,
+                   mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
         ++ctx->launches;
         for (int it = 0; it < mg->nu; ++it) {
             if (l == 0) {
                 SHL_TRY(fine_apply(L.x, L.t));
                 if (it == mg->nu - 1 && (fuse & kVcLastExternal)) break;
-                mg_jacobi_kernel<<<g, kBlk, 0, s>>>(L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
+                pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
                 ++ctx->launches;
             } else {
                 sweep(L, 2);
@@ -956,7 +979,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                     ++updates;
                     reliable_fold_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, x64, mask);
                     ++ctx->launches;
-                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, mask));
                     reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, r64, mask, restart, rr_true);
                     ++ctx->launches;
                     if (use_mg) {  // direction restarts from the preconditioned true residual

@@ -160,6 +160,7 @@ __device__ inline void case_pq_all(const ApplyDot &ad, double (&pq)[6]) {
 // stiffness apply's deferred per-CTA partials; a non-positive or non-finite
 // p.q stops the case with a numeric error.
 __global__ void pcg_alpha_kernel(PcgState *st, ApplyDot ad) {
+    pdl_enter();
     if (st->nactive == 0) return;
     double pq[6];
     case_pq_all(ad, pq);
@@ -200,6 +201,7 @@ struct FineJacobi {
 // Last block: iteration count, convergence and budget tests, nactive.
 template <typename T, int V, bool MG>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kernel(VecArgs<T> a, VecGeom g, FineJacobi fj) {
+    pdl_enter();
     PcgState *st = a.st;
     if (st->nactive == 0) return;  // uniform: the solve has finished
     const int k = blockIdx.x / g.bpk, j = blockIdx.x - k * g.bpk;
@@ -296,6 +298,7 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kerne
 template <int V>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_jacobi_rz_kernel(VecArgs<float> a, VecGeom g, FineJacobi fj,
                                                                     const float *__restrict__ t) {
+    pdl_enter();
     PcgState *st = a.st;
     if (st->nactive == 0) return;
     const int k = blockIdx.x / g.bpk, j = blockIdx.x - k * g.bpk;
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_jacobi_rz_ke
 // p = z + beta p (multigrid) or p = D^-1 r + beta p (point Jacobi), active cases.
 template <typename T, int V>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_direction_kernel(VecArgs<T> a, VecGeom g) {
+    pdl_enter();
     PcgState *st = a.st;
     if (st->nactive == 0) return;
     const int k = blockIdx.x / g.bpk, j = blockIdx.x - k * g.bpk;
