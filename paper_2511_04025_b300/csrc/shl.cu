@@ -708,22 +708,36 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             Lc[(size_t)i * m + j] = v / ljj;
         }
     }
-    std::vector<float> Ainv((size_t)n3 * n3, 0.0f);
-    std::vector<double> col(m);
-    for (int c = 0; c < m; ++c) {
-        for (int i = 0; i < m; ++i) col[i] = (i == c) ? 1.0 : 0.0;
-        for (int i = 0; i < m; ++i) {  // L y = e_c
-            double v = col[i];
-            for (int k = 0; k < i; ++k) v -= Lc[(size_t)i * m + k] * col[k];
-            col[i] = v / Lc[(size_t)i * m + i];
+    // A^-1 = L^-T L^-1: Y = L^-1 (lower triangular) by row operations, then
+    // A^-1 = Y^T Y accumulated row by row (unit-stride inner loops throughout)
+    std::vector<double> Y((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) {  // row i of L Y = I: Y[i][:i+1] = (e_i - sum_k<i L[i][k] Y[k]) / L[i][i]
+        double *yi = &Y[(size_t)i * m];
+        yi[i] = 1.0;
+        for (int k = 0; k < i; ++k) {
+            const double lik = Lc[(size_t)i * m + k];
+            const double *yk = &Y[(size_t)k * m];
+            for (int c = 0; c <= k; ++c) yi[c] -= lik * yk[c];
         }
-        for (int i = m - 1; i >= 0; --i) {  // L^T x = y
-            double v = col[i];
-            for (int k = i + 1; k < m; ++k) v -= Lc[(size_t)k * m + i] * col[k];
-            col[i] = v / Lc[(size_t)i * m + i];
-        }
-        for (int i = 0; i < m; ++i) Ainv[(size_t)(i + 3) * n3 + (c + 3)] = (float)col[i];
+        const double inv = 1.0 / Lc[(size_t)i * m + i];
+        for (int c = 0; c <= i; ++c) yi[c] *= inv;
     }
+    std::vector<double> G((size_t)m * m, 0.0);  // lower triangle of Y^T Y
+    for (int i = 0; i < m; ++i) {
+        const double *yi = &Y[(size_t)i * m];
+        for (int a = 0; a <= i; ++a) {
+            const double ya = yi[a];
+            double *ga = &G[(size_t)a * m];
+            for (int b = 0; b <= a; ++b) ga[b] += ya * yi[b];
+        }
+    }
+    std::vector<float> Ainv((size_t)n3 * n3, 0.0f);
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b <= a; ++b) {
+            const float v = (float)G[(size_t)a * m + b];
+            Ainv[(size_t)(a + 3) * n3 + (b + 3)] = v;
+            Ainv[(size_t)(b + 3) * n3 + (a + 3)] = v;
+        }
     SHL_TRY(ws_get_t(ctx, "mg_Ainv", (size_t)n3 * n3, &mg->Ainv));
     SHL_CUDA(ctx, cudaMemcpyAsync(mg->Ainv, Ainv.data(), Ainv.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
