@@ -74,8 +74,21 @@ inline void voigt_unit_strain(int k, double eps[3][3]) {
         eps[a[k]][b[k]] = eps[b[k]][a[k]] = 0.5;
 }
 
-// Builds the operator; returns the largest off-block entry of G relative to
-// max |G| (round-off level when the block structure holds).
+// Non-zero pattern of the transformed blocks G[c][i][j] of the isotropic
+// hex8 element (the same for every Poisson ratio; at nu = 0 some entries
+// vanish as well): row i of block c as a bit mask over j.  45 of the 72
+// block entries; the rows of the three translation modes are zero (a rigid
+// translation carries no force).  build_elem_op checks it.
+__host__ __device__ constexpr bool g_nz(int c, int i, int j) {
+    constexpr unsigned char rows[8][3] = {{7, 7, 7}, {0, 6, 6}, {5, 0, 5}, {3, 3, 4},
+                                          {3, 3, 0}, {5, 2, 5}, {1, 6, 6}, {7, 7, 7}};
+    return (rows[c][i] >> j) & 1;
+}
+__host__ __device__ constexpr bool g_row_nz(int c, int i) { return g_nz(c, i, 0) || g_nz(c, i, 1) || g_nz(c, i, 2); }
+
+// Builds the operator; returns the largest entry of G outside its block and
+// non-zero pattern relative to max |G| (round-off level when the structure
+// holds).
 template <typename T>
 inline double build_elem_op(double nu, int r, ElemOp<T> *op) {
     double Ku[24][24];
@@ -101,8 +114,9 @@ inline double build_elem_op(double nu, int r, ElemOp<T> *op) {
         for (int i = 0; i < 3; ++i)
             for (int n = 0; n < 8; ++n)
                 for (int j = 0; j < 3; ++j) {
-                    const bool in_block = ((m ^ (1 << i)) == (n ^ (1 << j)));
-                    if (!in_block) off = std::fmax(off, std::fabs(Gf[3 * m + i][3 * n + j]));
+                    const int cb = m ^ (1 << i);  // block of row (m, i)
+                    const bool in_block = cb == (n ^ (1 << j));
+                    if (!in_block || !g_nz(cb, i, j)) off = std::fmax(off, std::fabs(Gf[3 * m + i][3 * n + j]));
                 }
     for (int c = 0; c < 8; ++c)
         for (int i = 0; i < 3; ++i)
@@ -154,15 +168,29 @@ __device__ __forceinline__ void wht8(T (&v)[8]) {
             }
 }
 
-// y = scale * G u in the transformed basis (u, y: [component][mode]).
+// y = scale * G u in the transformed basis (u, y: [component][mode]); only
+// the entries of the non-zero pattern are multiplied (45 of 72).
 template <typename T>
 __device__ __forceinline__ void block_apply(const ElemOp<T> &op, const T (&u)[3][8], T (&y)[3][8], T scale) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const T a0 = u[0][c ^ 1], a1 = u[1][c ^ 2], a2 = u[2][c ^ 4];
-        y[0][c ^ 1] = scale * (op.G[c][0][0] * a0 + op.G[c][0][1] * a1 + op.G[c][0][2] * a2);
-        y[1][c ^ 2] = scale * (op.G[c][1][0] * a0 + op.G[c][1][1] * a1 + op.G[c][1][2] * a2);
-        y[2][c ^ 4] = scale * (op.G[c][2][0] * a0 + op.G[c][2][1] * a1 + op.G[c][2][2] * a2);
+        const T a[3] = {u[0][c ^ 1], u[1][c ^ 2], u[2][c ^ 4]};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (!g_row_nz(c, i)) {
+                y[i][c ^ (1 << i)] = T(0);
+                continue;
+            }
+            T s = T(0);
+            bool first = true;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (g_nz(c, i, j)) {
+                    s = first ? op.G[c][i][j] * a[j] : s + op.G[c][i][j] * a[j];
+                    first = false;
+                }
+            y[i][c ^ (1 << i)] = scale * s;
+        }
     }
 }
 
