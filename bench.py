@@ -12,6 +12,7 @@ one process per GPU, weak scaling, no data-path collective.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl shl|reference]
   python bench.py --serve [--requests R] [--slots S]   # serving stream
   python bench.py --kernel apply [--r R]              # dominant kernel alone
+  python bench.py --field                              # field on the paper's Table 1 shapes
 """
 from __future__ import annotations
 
@@ -231,6 +232,56 @@ def run_kernel(args):
     print(json.dumps(line), flush=True)
 
 
+# Table 1 of the paper: field evaluation shapes (r, 2N) and the H200 times it
+# reports (context only; another machine, another method).
+FIELD_SHAPES = [(64, 32), (128, 32), (256, 32), (256, 64), (256, 128), (256, 256)]
+FIELD_PAPER_H200_MS = {(64, 32): 0.7, (128, 32): 5.5, (256, 32): 43.0, (256, 64): 85.8, (256, 128): 171.7,
+                       (256, 256): 347.2}
+FP64_NOMINAL_GFLOPS = 1250.0  # B300 FP64 (non-tensor), nominal
+
+
+def run_field(args):
+    """Field throughput on the paper's Table 1 shapes: F and grad F of 2N
+    balanced charges on the r^3 voxel centres (K = 3), FP64, CUDA events on
+    the launch stream.  The separable evaluation costs 4(2K+1) FMAs per voxel
+    after per-plane and per-line contractions, independent of 2N."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    torch.cuda.set_device(0)
+    rows = []
+    with shl.Context(0) as ctx:
+        h = ctx.handle
+        stream = torch.cuda.Stream()
+        for r, n in FIELD_SHAPES:
+            d = inputs.random_design(7, n, 0.1)
+            F = torch.empty(r ** 3, dtype=torch.float64, device="cuda")
+            gF = torch.empty(r ** 3, 3, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                shl.shl_field(h, d, r, F, gF, stream=stream)
+            reps = 10
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(40_000_000)
+            e0.record(stream)
+            for _ in range(reps):
+                shl.shl_field(h, d, r, F, gF, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            flops = 2.0 * 4 * (2 * d.K + 1) * r ** 3
+            rows.append({"r": r, "charges": n, "ms": ms, "paper_h200_ms": FIELD_PAPER_H200_MS[(r, n)],
+                         "fp64_gflops": flops / ms / 1e6, "out_gbs": 32.0 * r ** 3 / ms / 1e6})
+    last = rows[-1]
+    line = {"metric": "field evaluation time, F and grad F (r=256, 2N=256)", "value": last["ms"], "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "field (paper Table 1 shapes)", "K": 3},
+            "roofline": {"bound": "fp64", "achieved": last["fp64_gflops"], "peak": FP64_NOMINAL_GFLOPS,
+                         "unit": "GFLOP/s", "frac": last["fp64_gflops"] / FP64_NOMINAL_GFLOPS,
+                         "peak_kind": "nominal", "traffic": None},
+            "shapes": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: a Poisson request stream (grids 32^3/64^3/96^3 at
     0.50/0.35/0.15, 8-64 charges, 3-20 % solid, 25 % warm-start follow-ups).
@@ -312,6 +363,7 @@ def main():
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--kernel", choices=["apply"], help="time the dominant kernel alone instead of the bench")
+    ap.add_argument("--field", action="store_true", help="field throughput on the paper's Table 1 shapes")
     ap.add_argument("--r", type=int, default=0, help="grid size for --kernel (default: the workload's)")
     ap.add_argument("--launches", type=int, default=40, help="timed launches for --kernel")
     args = ap.parse_args()
@@ -319,6 +371,8 @@ def main():
         return run_reference(args)
     if args.kernel:
         return run_kernel(args)
+    if args.field:
+        return run_field(args)
     if args.serve:
         return run_serve(args)
 

@@ -235,3 +235,17 @@ def test_invalid_arguments_rejected(ctx):
     with pytest.raises(shl.ShlError) as e:
         shl.shl_homogenize(ctx, d, 16, shl.default_solve_opts(nu=0.5))
     assert e.value.status == shl.SHL_EINVAL
+
+
+@pytest.mark.parametrize("r,n", [(16, 256), (24, 64)])
+def test_field_many_charges_matches_oracle(ctx, r, n):
+    """Table 1's charge counts (2N up to 256): the separable evaluation on the
+    GPU against the oracle's direct sum over charges."""
+    d = inputs.random_design(11, n, 0.1)
+    F = torch.empty(r ** 3, dtype=torch.float64, device=DEV)
+    gF = torch.empty(r ** 3, 3, dtype=torch.float64, device=DEV)
+    shl.shl_field(ctx, d, r, F, gF)
+    torch.cuda.synchronize()
+    Fo, gFo = oracle.field_grid(d, r)
+    assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-12 * np.abs(Fo).max()
+    assert np.abs(gF.cpu().numpy() - gFo).max() <= 1e-12 * np.abs(gFo).max()
