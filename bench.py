@@ -1,8 +1,12 @@
 """Benchmark: homogenised designs/sec (6x6 C^H) on synthetic shell designs.
 
 One step = the whole path for one design: field -> distance -> threshold ->
-mask -> six periodic cell problems (FP32 PCG + FP64 residual refinement to a
-1e-10 relative residual) -> C^H, through the C-ABI call shl_homogenize.
+mask -> six periodic cell problems (FP32 PCG with a multigrid preconditioner
++ FP64 residual refinement to a relative residual of --tol, default 1e-7) ->
+C^H, through the C-ABI call shl_homogenize.  The metric asks C^H within 1e-4
+(relative entry error); every timed design is solved again afterwards,
+untimed, by the plain FP64 GPU path to 1e-11 and the largest entry error is
+reported ("accuracy").
 
 Default workload: 64^3 grid, 32 charges uniform in the cell with magnitudes
 N(0,1), 8 % solid volume (seeded synthetic designs; the paper's datasets are
@@ -293,7 +297,7 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     reqs = inputs.serving_stream(seed=0, n_requests=args.requests, rate_hz=1.0)
-    opts = lambda warm: shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10, warm_start=int(warm))
+    opts = lambda warm: shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=args.tol, warm_start=int(warm))
 
     def replay(ctx, scale):
         t0 = time.perf_counter()
@@ -339,7 +343,7 @@ def run_serve(args):
         "unit": "designs/s", "n_gpus": 1, "steps": len(reqs), "warmup": 3, "ms_per_step": 1e3 * wall2 / len(reqs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": "serve", "requests": len(reqs), "slots": args.slots, "grids": "32/64/96 @ .50/.35/.15",
-                   "tol": 1e-10, "warm_start_share": float(np.mean([q.follow_up_of >= 0 for q in reqs]))},
+                   "tol": args.tol, "warm_start_share": float(np.mean([q.follow_up_of >= 0 for q in reqs]))},
         "latency_s": {"p50": p50, "p99": p99, "p50_64": p50_64, "p99_64": p99_64},
         "burst": {"designs_per_s": X, "latency_p50": lat(res1)[0], "latency_p99": lat(res1)[1]},
         "warm_hits": int(sum(1 for _, x in res2 if x["warm"])), "all_converged": ok,
@@ -359,6 +363,8 @@ def main():
     ap.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-7,
+                    help="relative residual of the cell problems (the metric asks C^H within 1e-4; 1e-7 gives <= 4e-7)")
     ap.add_argument("--serve", action="store_true", help="serving workload (Poisson stream) instead of the bench")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--slots", type=int, default=16)
@@ -383,7 +389,7 @@ def main():
     torch.cuda.set_device(local)
     gen, r, desc = WORKLOADS[args.workload]
     prec = shl.SHL_FP32_REFINE if args.precision == "fp32r" else shl.SHL_FP64
-    opts = shl.default_solve_opts(precision=prec, tol=1e-10)
+    opts = shl.default_solve_opts(precision=prec, tol=args.tol)
     ctx = shl.Context(local)
     h = ctx.handle
     stream = torch.cuda.Stream()
@@ -397,6 +403,7 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall = []
     stats = []
+    Cs = []
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -409,6 +416,7 @@ def main():
             t0 = time.perf_counter()
             ev[k][0].record(stream)
             C, st = shl.shl_homogenize(h, designs[args.warmup + k], r, opts, stream=stream)
+            Cs.append(C)
             ev[k][1].record(stream)
             stream.synchronize()
             wall.append(time.perf_counter() - t0)
@@ -430,19 +438,32 @@ def main():
     apply_s = time_apply(h, r, designs[-1], stream)
     roofline = apply_roofline(r, apply_s)
 
+    # accuracy of every timed design (untimed): C^H against the plain FP64 GPU
+    # path solved to 1e-11, entry error relative to max(|C_ij|, 1e-2 max|C|)
+    ref = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-11)
+    acc = 0.0
+    for k in range(args.steps):
+        Cr, _ = shl.shl_homogenize(h, designs[args.warmup + k], r, ref, stream=stream)
+        acc = max(acc, float(np.max(np.abs(Cs[k] - Cr) / np.maximum(np.abs(Cr), 1e-2 * np.abs(Cr).max()))))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([acc], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        acc = float(t[0])
+    accuracy = {"chom_entry_err_max": acc, "bound": 1e-4, "designs": args.steps * world,
+                "reference": "FP64 GPU path, tol 1e-11"}
+
+    # the plain FP64 GPU path on the last design at the same tolerance (equal accuracy)
     compare = None
     if not args.no_compare and prec == shl.SHL_FP32_REFINE and rank == 0:
-        o64 = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-10)
+        o64 = shl.default_solve_opts(precision=shl.SHL_FP64, tol=args.tol)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         C64, st64 = shl.shl_homogenize(h, designs[-1], r, o64, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         s64 = e0.elapsed_time(e1) / 1e3
-        Cm = C
-        err = float(np.max(np.abs(Cm - C64) / np.maximum(np.abs(C64), 1e-2 * np.abs(C64).max())))
-        compare = {"fp64_designs_per_s": 1.0 / s64, "fp64_iters": max(st64["iters"]),
-                   "fp32r_vs_fp64_entry_err": err}
+        compare = {"fp64_designs_per_s": 1.0 / s64, "fp64_iters": max(st64["iters"]), "tol": args.tol}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -457,14 +478,14 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "r": r, "precision": args.precision,
-                       "tol": 1e-10, "l2": "flushed between steps", "parallelism": f"replicas x{world}"},
+                       "tol": args.tol, "l2": "flushed between steps", "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e, "unit": "designs/s", "h2d_bytes_per_step": int(d0.pos.nbytes + d0.q.nbytes),
                     "d2h_bytes_per_step": 36 * 8},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(c1 - c0),
             "solver": {"iters_max": [max(s["iters"]) for s in stats], "n_refine": [s["n_refine"] for s in stats],
                        "relres_max": max(max(s["relres"]) for s in stats)},
-            "compare": compare,
+            "accuracy": accuracy, "compare": compare,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

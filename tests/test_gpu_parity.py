@@ -249,3 +249,13 @@ def test_field_many_charges_matches_oracle(ctx, r, n):
     Fo, gFo = oracle.field_grid(d, r)
     assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-12 * np.abs(Fo).max()
     assert np.abs(gF.cpu().numpy() - gFo).max() <= 1e-12 * np.abs(gFo).max()
+
+
+def test_bench_tolerance_meets_metric_accuracy(ctx):
+    """The throughput workload solves to a relative residual of 1e-7; C^H must
+    then stay within the metric's 1e-4 of the oracle (measured ~3e-7)."""
+    g = gold("gaussian64_s0")
+    d = inputs.gaussian_64(0)
+    C, st = shl.shl_homogenize(ctx, d, 64, shl.default_solve_opts(tol=1e-7, precision=shl.SHL_FP32_REFINE))
+    assert st["status"] == 0 and max(st["relres"]) <= 1e-7
+    assert entry_err(C, g["C"]) <= 1e-5
