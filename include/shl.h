@@ -115,7 +115,7 @@ typedef struct {
  *   density        SHL_MASK: binary rho; SHL_SMOOTH: rho = 1/(1+exp(-kappa(t-d)))
  *   kappa          logistic sharpness; <= 0 selects ln(9) * r (two-voxel rise)
  *   inner_tol      FP32_REFINE: residual reduction between reliable updates
- *                  (<= 0 selects 1e-3)
+ *                  (<= 0 selects 1e-4)
  *   warm_start     use the displacements passed in (shl_solve) or kept for the
  *                  session (serving) as the initial guess
  *   precond        SHL_PRECOND_MG (default): geometric multigrid V-cycle

@@ -899,7 +899,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         SHL_TRY(ws_get_t(ctx, "refine_scale", 8, &one));
         const double h_one[8] = {1, 1, 1, 1, 1, 1, 1, 1};
         SHL_CUDA(ctx, cudaMemcpyAsync(one, h_one, sizeof(h_one), cudaMemcpyHostToDevice, s));
-        const double delta = o->inner_tol > 0.0 ? o->inner_tol : 1e-3;
+        const double delta = o->inner_tol > 0.0 ? o->inner_tol : 1e-4;
         // r64 = f - K x64 (pinned); r32 = float(r64); x32 = 0
         SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
         refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, one, 0x3f, b.r, b.x);
@@ -1302,7 +1302,7 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->precision = SHL_FP64;
     o->density = SHL_MASK;
     o->kappa = 0.0;
-    o->inner_tol = 1e-3;
+    o->inner_tol = 1e-4;
     o->precond = SHL_PRECOND_MG;
     o->mg_nu = 1;
     o->mg_omega = 1.4;
