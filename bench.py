@@ -17,6 +17,7 @@ one process per GPU, weak scaling, no data-path collective.
   python bench.py --serve [--requests R] [--slots S]   # serving stream
   python bench.py --kernel apply [--r R]              # dominant kernel alone
   python bench.py --field                              # field on the paper's Table 1 shapes
+  python bench.py --grad [--batch B]                   # inverse-design gradients at 64^3
 """
 from __future__ import annotations
 
@@ -286,6 +287,72 @@ def run_field(args):
     print(json.dumps(line), flush=True)
 
 
+def cubic_symmetry_err(C):
+    """Largest deviation of C^H from cubic symmetry (C11=C22=C33, C12=C13=C23,
+    C44=C55=C66, all other entries zero), relative to max |C|."""
+    s = np.abs(C).max()
+    dev = [C[0, 0] - C[1, 1], C[0, 0] - C[2, 2], C[0, 1] - C[0, 2], C[0, 1] - C[1, 2], C[3, 3] - C[4, 4],
+           C[3, 3] - C[5, 5]]
+    cubic = {(i, j) for i in range(3) for j in range(3)} | {(3, 3), (4, 4), (5, 5)}
+    dev += [C[i, j] for i in range(6) for j in range(6) if (i, j) not in cubic]
+    return float(np.max(np.abs(dev)) / s)
+
+
+def run_grad(args):
+    """Inverse-design gradients: a batch of designs at 64^3 (24 balanced
+    charges, 10 % solid), objective E = sum (C^H - C_t)^2 with C_t isotropic
+    (bulk 0.05, shear 0.02); forward and backward through the
+    torch.autograd.Function over the adjoint (smoothed density, FP32 + FP64
+    refinement at --tol; the backward starts from the forward's displacements).
+    The thickness of each design is selected from its volume fraction first
+    and then held fixed.  Accuracy: the first design's gradient against the
+    FP64 path at 1e-12."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    from paper_2511_04025_b300.autograd import HomogenizeFn
+    torch.cuda.set_device(0)
+    r, batch, warm = 64, args.batch, 2
+    designs = [inputs.gradient_64(1000 + i) for i in range(batch + warm)]
+    Ct = torch.tensor(inputs.isotropic_target())
+    o = shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=args.tol, density=shl.SHL_SMOOTH)
+    with shl.Context(0) as ctx:
+        h = ctx.handle
+        ts = [shl.shl_voxelize(h, d, r)["t"] for d in designs]
+
+        def one(d, t):
+            pos = torch.tensor(d.pos, requires_grad=True)
+            q = torch.tensor(d.q, requires_grad=True)
+            iso = torch.tensor(d.iso, dtype=torch.float64, requires_grad=True)
+            tt = torch.tensor(t, dtype=torch.float64, requires_grad=True)
+            C = HomogenizeFn.apply(pos, q, iso, tt, h, r, d.K, None, o)
+            loss = ((C - Ct) ** 2).sum()
+            loss.backward()
+            return C.detach().numpy(), pos.grad.numpy(), q.grad.numpy(), float(tt.grad)
+
+        for k in range(warm):
+            one(designs[k], ts[k])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = [one(designs[warm + k], ts[warm + k]) for k in range(batch)]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        d0, t_0 = designs[warm], ts[warm]
+        o64 = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-12, density=shl.SHL_SMOOTH)
+        C64 = shl.shl_homogenize(h, d0.copy(t=t_0), r, o64)[0]
+        ref = shl.shl_grad(h, d0, r, o64, 2.0 * (C64 - Ct.numpy()), t=t_0)
+    C0, gp, gq, gt = outs[0]
+    scale = max(np.abs(ref["g_pos"]).max(), np.abs(ref["g_q"]).max(), abs(ref["g_t"]))
+    gerr = max(np.abs(gp - ref["g_pos"]).max(), np.abs(gq - ref["g_q"]).max(), abs(gt - ref["g_t"])) / scale
+    line = {"metric": "inverse-design gradients/sec (64^3, forward + adjoint through autograd)",
+            "value": batch / wall, "unit": "gradients/s", "n_gpus": 1, "steps": batch, "warmup": warm,
+            "ms_per_step": 1e3 * wall / batch, "higher_is_better": True, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "gradient64", "designs": batch, "charges": 24, "vf": 0.10, "tol": args.tol,
+                       "density": "smooth (logistic, kappa = ln 9 r)"},
+            "accuracy": {"grad_rel_err": float(gerr), "reference": "FP64 GPU path, tol 1e-12 (first design)"},
+            "e2e": {"value": batch / wall, "unit": "gradients/s", "note": "host wall clock, per-design sync"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: a Poisson request stream (grids 32^3/64^3/96^3 at
     0.50/0.35/0.15, 8-64 charges, 3-20 % solid, 25 % warm-start follow-ups).
@@ -370,6 +437,8 @@ def main():
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--kernel", choices=["apply"], help="time the dominant kernel alone instead of the bench")
     ap.add_argument("--field", action="store_true", help="field throughput on the paper's Table 1 shapes")
+    ap.add_argument("--grad", action="store_true", help="inverse-design gradients on a batch of 64^3 designs")
+    ap.add_argument("--batch", type=int, default=64, help="designs per gradient batch (--grad)")
     ap.add_argument("--r", type=int, default=0, help="grid size for --kernel (default: the workload's)")
     ap.add_argument("--launches", type=int, default=40, help="timed launches for --kernel")
     args = ap.parse_args()
@@ -379,6 +448,8 @@ def main():
         return run_kernel(args)
     if args.field:
         return run_field(args)
+    if args.grad:
+        return run_grad(args)
     if args.serve:
         return run_serve(args)
 
@@ -452,6 +523,8 @@ def main():
         acc = float(t[0])
     accuracy = {"chom_entry_err_max": acc, "bound": 1e-4, "designs": args.steps * world,
                 "reference": "FP64 GPU path, tol 1e-11"}
+    if args.workload == "cubic128":
+        accuracy["cubic_symmetry_err_max"] = max(cubic_symmetry_err(C) for C in Cs)
 
     # the plain FP64 GPU path on the last design at the same tolerance (equal accuracy)
     compare = None

@@ -259,3 +259,18 @@ def test_bench_tolerance_meets_metric_accuracy(ctx):
     C, st = shl.shl_homogenize(ctx, d, 64, shl.default_solve_opts(tol=1e-7, precision=shl.SHL_FP32_REFINE))
     assert st["status"] == 0 and max(st["relres"]) <= 1e-7
     assert entry_err(C, g["C"]) <= 1e-5
+
+
+def test_cubic128_chom_has_cubic_symmetry(ctx):
+    """The 128^3 O_h design at full size: C^H is cubic (C11 = C22 = C33,
+    C12 = C13 = C23, C44 = C55 = C66, the rest zero) to solver accuracy."""
+    C, st = shl.shl_homogenize(ctx, inputs.cubic_128(0), 128,
+                               shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP32_REFINE))
+    assert st["status"] == 0
+    s = np.abs(C).max()
+    dev = [C[0, 0] - C[1, 1], C[0, 0] - C[2, 2], C[0, 1] - C[0, 2], C[0, 1] - C[1, 2], C[3, 3] - C[4, 4],
+           C[3, 3] - C[5, 5]]
+    cubic = {(i, j) for i in range(3) for j in range(3)} | {(3, 3), (4, 4), (5, 5)}
+    dev += [C[i, j] for i in range(6) for j in range(6) if (i, j) not in cubic]
+    assert np.max(np.abs(dev)) <= 1e-8 * s
+    assert np.abs(C - C.T).max() <= 1e-12 * s
