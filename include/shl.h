@@ -236,8 +236,10 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
                    shl_stats *st, void *stream);
 
 /*
- * Hand-written adjoint (Eq. chain): for an objective E(C^H) with dE/dC^H =
- * dE_dC (36 host doubles, row-major), the gradient with respect to the charge
+ * Hand-written adjoint (Eq. chain): for an objective E(C^H, V) with dE/dC^H =
+ * dE_dC (36 host doubles, row-major) and dE/dV = dE_dV, V = (1/r^3) sum_e
+ * rho_e the solid volume fraction of the smoothed density (the objectives of
+ * Sec. 5.3 divide stiffness by it), the gradient with respect to the charge
  * positions (g_pos, n x 3), magnitudes (g_q, n), iso-level (g_iso), shell
  * half-thickness (g_t) and spectral weights (g_alpha, (K+1)^3 or NULL),
  * through the smoothed density rho_e = 1/(1+exp(-kappa(t - d_e))) with the
@@ -248,12 +250,13 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
  * the field.  When t comes from d->vf it is selected first and then held
  * fixed.  C_out (36) receives C^H.  u_dev (18 SoA planes of doubles, may be
  * NULL) receives the displacements and, with o->warm_start, seeds the solve
- * (pass the forward's u_dev to make a backward pass solve-free).  Any output
- * pointer may be NULL.
+ * (pass the forward's u_dev to make a backward pass solve-free).  V_out
+ * receives V.  Any output pointer may be NULL; SHL_EINVAL for a non-finite
+ * dE_dC or dE_dV.
  */
 int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, const double *dE_dC,
-             double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t, double *g_alpha,
-             shl_stats *st, void *stream);
+             double dE_dV, double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t,
+             double *g_alpha, double *V_out, shl_stats *st, void *stream);
 
 /* n designs, each on its own r[i]^3 grid; C_out: n x 36; st: n records or NULL. */
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,

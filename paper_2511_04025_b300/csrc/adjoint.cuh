@@ -21,19 +21,21 @@ struct SeedArgs {
     double *F;    // in: F, out: Fbar
     double *gF;   // in: grad F (x,y,z per voxel), out: gFbar
     const double *rho;  // beta_e
-    const double *g;    // dE/drho_e
+    const double *g;    // dE/drho_e through C^H
+    double gV;          // dE/dV / N: V = (1/N) sum_e rho_e adds this to every dE/drho_e
     double iso, kappa;
-    double *partial;    // [nblocks][2]
+    double *partial;    // [nblocks][3]
     unsigned *ticket;
-    double *out;        // [0] dE/dt, [1] dE/dc
+    double *out;        // [0] dE/dt, [1] dE/dc, [2] V
 };
 
 __global__ void adj_seed_kernel(SeedArgs a) {
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < a.N; e += (size_t)gridDim.x * blockDim.x) {
         const double b = a.rho[e];
         const double db = a.kappa * b * (1.0 - b);
-        const double ge = a.g[e];
+        const double ge = a.g[e] + a.gV;
+        acc[2] += b;
         acc[0] += ge * db;
         const double dEdd = -ge * db;
         const double F = a.F[e] - a.iso;
@@ -51,13 +53,14 @@ __global__ void adj_seed_kernel(SeedArgs a) {
         a.gF[3 * e + 1] = cg * gy;
         a.gF[3 * e + 2] = cg * gz;
     }
-    block_reduce_store<2>(acc, a.partial, blockIdx.x);
+    block_reduce_store<3>(acc, a.partial, blockIdx.x);
     if (!last_block_ticket(a.ticket, gridDim.x)) return;
-    __shared__ double tot[2];
-    sum_partials_ordered<2>(a.partial, gridDim.x, tot);
+    __shared__ double tot[3];
+    sum_partials_ordered<3>(a.partial, gridDim.x, tot);
     if (threadIdx.x == 0) {
         a.out[0] = tot[0];
         a.out[1] = tot[1];
+        a.out[2] = tot[2] / (double)a.N;
     }
 }
 

@@ -1171,12 +1171,13 @@ inline size_t design_footprint(int r, const shl_solve_opts *o) {
     return N * per + ((size_t)8 << 20);
 }
 
-// Gradient of an objective E(C^H) with dE/dC^H = dEdC (host, 36) w.r.t.
-// charge positions/magnitudes, iso-level, half-thickness and alpha (Eq. chain),
+// Gradient of an objective E(C^H, V) with dE/dC^H = dEdC (host, 36) and
+// dE/dV = dEdV, V the mean smoothed occupancy, w.r.t. charge
+// positions/magnitudes, iso-level, half-thickness and alpha (Eq. chain),
 // through the smoothed density.  Arguments validated, lock held.
 inline int grad_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_opts *o, const double *dEdC,
-                     double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t,
-                     double *g_alpha, shl_stats *st, cudaStream_t s) {
+                     double dEdV, double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso,
+                     double *g_t, double *g_alpha, double *V_out, shl_stats *st, cudaStream_t s) {
     const size_t N = (size_t)r * r * r;
     const int nb = 2 * d->K + 1;
     double *F = nullptr, *gF = nullptr, *dd = nullptr, *rho = nullptr, *g = nullptr, *QR = nullptr, *Abar = nullptr,
@@ -1231,9 +1232,9 @@ inline int grad_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_o
     }
     // seeds for F, grad F; dE/dt, dE/dc
     const int gs = grid1d(N, kBlk, 148 * 4);
-    SHL_TRY(ws_get_t(ctx, "adj_partial", (size_t)gs * 2, &partial));
+    SHL_TRY(ws_get_t(ctx, "adj_partial", (size_t)gs * 3, &partial));
     SHL_TRY(ws_get_t(ctx, "adj_ticket", 1, &ticket));
-    SeedArgs sa{N, F, gF, rho, g, d->iso, kappa, partial, ticket, gout};
+    SeedArgs sa{N, F, gF, rho, g, dEdV / (double)N, d->iso, kappa, partial, ticket, gout};
     adj_seed_kernel<<<gs, kBlk, 0, s>>>(sa);
     ++ctx->launches;
     // back through the separable field to the coefficient tensor and the charges
@@ -1256,15 +1257,16 @@ inline int grad_impl(shl_ctx *ctx, const shl_design *d, int r, const shl_solve_o
     }
     SHL_CUDA(ctx, cudaGetLastError());
     std::vector<double> hg((size_t)4 * d->n + na);
-    double ho[2];
+    double ho[3];
     SHL_CUDA(ctx, cudaMemcpyAsync(hg.data(), gp, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    SHL_CUDA(ctx, cudaMemcpyAsync(ho, gout, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaMemcpyAsync(ho, gout, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
     if (g_pos) std::memcpy(g_pos, hg.data(), sizeof(double) * 3 * d->n);
     if (g_q) std::memcpy(g_q, hg.data() + 3 * d->n, sizeof(double) * d->n);
     if (g_alpha) std::memcpy(g_alpha, hg.data() + 4 * d->n, sizeof(double) * na);
     if (g_t) *g_t = ho[0];
     if (g_iso) *g_iso = ho[1];
+    if (V_out) *V_out = ho[2];
     return rc;
 }
 
@@ -1462,8 +1464,8 @@ int shl_homogenize(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve
 }
 
 int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts *o, const double *dE_dC,
-             double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t, double *g_alpha,
-             shl_stats *st, void *stream) {
+             double dE_dV, double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t,
+             double *g_alpha, double *V_out, shl_stats *st, void *stream) {
     if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     SHL_TRY(validate_solve_opts(ctx, o));
@@ -1473,8 +1475,10 @@ int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts 
     if (!dE_dC) return set_err(ctx, SHL_EINVAL, "dE_dC is NULL");
     for (int i = 0; i < 36; ++i)
         if (!std::isfinite(dE_dC[i])) return set_err(ctx, SHL_EINVAL, "non-finite dE_dC");
+    if (!std::isfinite(dE_dV)) return set_err(ctx, SHL_EINVAL, "non-finite dE_dV");
     cudaSetDevice(ctx->device);
-    return grad_impl(ctx, d, r, o, dE_dC, u_dev, C_out, g_pos, g_q, g_iso, g_t, g_alpha, st, pick_stream(ctx, stream));
+    return grad_impl(ctx, d, r, o, dE_dC, dE_dV, u_dev, C_out, g_pos, g_q, g_iso, g_t, g_alpha, V_out, st,
+                     pick_stream(ctx, stream));
 }
 
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,

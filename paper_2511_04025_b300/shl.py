@@ -104,7 +104,8 @@ SIGNATURES = {
     "shl_chom_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _vp, _vp, _vp]),
     "shl_grad": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32, ctypes.POINTER(shl_solve_opts), _dp,
-                                _vp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(shl_stats), _vp]),
+                                ctypes.c_double, _vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(shl_stats),
+                                _vp]),
     "shl_serve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(shl_request), ctypes.POINTER(ctypes.c_uint64)]),
     "shl_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(shl_result)]),
     "shl_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(shl_result)]),
@@ -274,25 +275,26 @@ def shl_chom_noalloc(r: int, u, C_dev, mask=None, rho=None, E=1.0, nu=0.3, E_voi
 
 
 def shl_grad(ctx, design, r: int, opts: shl_solve_opts, dEdC, u=None, t: Optional[float] = None,
-             want_alpha: bool = False, stream=None) -> dict:
-    """C^H and dE/d(positions, magnitudes, iso-level, thickness[, alpha]) for an
-    objective with dE/dC^H = dEdC (6x6), through the smoothed density."""
+             want_alpha: bool = False, dEdV: float = 0.0, stream=None) -> dict:
+    """C^H, the smoothed volume fraction V and dE/d(positions, magnitudes,
+    iso-level, thickness[, alpha]) for an objective with dE/dC^H = dEdC (6x6)
+    and dE/dV = dEdV, through the smoothed density."""
     d = DesignArg(design, t)
     n = d.pos.shape[0]
     G = np.ascontiguousarray(np.asarray(dEdC, dtype=np.float64).reshape(36))
     C = np.zeros(36)
     g_pos = np.zeros((n, 3))
     g_q = np.zeros(n)
-    g_iso, g_t = ctypes.c_double(), ctypes.c_double()
+    g_iso, g_t, V = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     g_alpha = np.zeros((design.K + 1) ** 3) if want_alpha else None
     st = shl_stats()
-    rc = lib().shl_grad(ctx, ctypes.byref(d.s), r, ctypes.byref(opts), G.ctypes.data_as(_dp), _ptr(u),
+    rc = lib().shl_grad(ctx, ctypes.byref(d.s), r, ctypes.byref(opts), G.ctypes.data_as(_dp), float(dEdV), _ptr(u),
                         C.ctypes.data_as(_dp), g_pos.ctypes.data_as(_dp), g_q.ctypes.data_as(_dp), ctypes.byref(g_iso),
-                        ctypes.byref(g_t), g_alpha.ctypes.data_as(_dp) if want_alpha else None, ctypes.byref(st),
-                        _stream(stream))
+                        ctypes.byref(g_t), g_alpha.ctypes.data_as(_dp) if want_alpha else None, ctypes.byref(V),
+                        ctypes.byref(st), _stream(stream))
     _check(ctx, rc, ok=(SHL_OK, SHL_ENOCONV))
-    return dict(C=C.reshape(6, 6), g_pos=g_pos, g_q=g_q, g_iso=g_iso.value, g_t=g_t.value, g_alpha=g_alpha,
-                stats=st.as_dict())
+    return dict(C=C.reshape(6, 6), V=V.value, g_pos=g_pos, g_q=g_q, g_iso=g_iso.value, g_t=g_t.value,
+                g_alpha=g_alpha, stats=st.as_dict())
 
 
 def shl_serve_submit(ctx, design, r: int, opts: shl_solve_opts, session: int = -1) -> int:
