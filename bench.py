@@ -156,6 +156,14 @@ def dist_setup(n_gpus):
     return rank, world, local
 
 
+def bench_config(args, r, desc, world):
+    """The workload the headline line is quoted on (both arms print it)."""
+    B = max(1, args.batch_designs)
+    return {"workload": args.workload, "desc": desc, "r": r, "precision": args.precision, "tol": args.tol,
+            "l2": "flushed between steps", "parallelism": f"replicas x{world}",
+            "batch": f"{B} designs per step, concurrent on {min(B, args.slots)} serving slots"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step a bounded sample."""
     rank, world, local = dist_setup(args.gpus)
@@ -177,7 +185,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "desc": desc, "r": r, "tol": 1e-12},
+            "config": bench_config(args, r, desc, world),
             "cpu_baseline": {"value": value, "unit": "designs/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "designs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -491,6 +499,9 @@ def main():
     ap.add_argument("--field", action="store_true", help="field throughput on the paper's Table 1 shapes")
     ap.add_argument("--grad", action="store_true", help="inverse-design gradients on a batch of 64^3 designs")
     ap.add_argument("--batch", type=int, default=64, help="designs per gradient batch (--grad)")
+    ap.add_argument("--batch-designs", type=int, default=1,
+                    help="designs per timed step, solved concurrently through shl_homogenize_batch (1: one at a time; "
+                         "one 64^3 or 128^3 design already saturates the GPU, so concurrency does not raise throughput)")
     ap.add_argument("--design", action="store_true", help="inverse-design driver at 64^3 (Keff by default)")
     ap.add_argument("--objective", default="Keff", choices=["Ex", "Cavg", "Keff", "Geff", "coupling", "isotropy"])
     ap.add_argument("--alpha-steps", type=int, default=4)
@@ -520,14 +531,25 @@ def main():
     gen, r, desc = WORKLOADS[args.workload]
     prec = shl.SHL_FP32_REFINE if args.precision == "fp32r" else shl.SHL_FP64
     opts = shl.default_solve_opts(precision=prec, tol=args.tol)
-    ctx = shl.Context(local)
+    ctx = shl.Context(local, max_batch=args.slots)
     h = ctx.handle
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
-    designs = [getattr(inputs, gen)(100000 * rank + i) for i in range(args.warmup + args.steps)]
+    B = max(1, args.batch_designs)
+    designs = [getattr(inputs, gen)(100000 * rank + i) for i in range((args.warmup + args.steps) * B)]
+    batches = [designs[k * B:(k + 1) * B] for k in range(args.warmup + args.steps)]
 
-    for i in range(args.warmup):
-        shl.shl_homogenize(h, designs[i], r, opts, stream=stream)
+    def solve(batch):
+        """One step: a batch of designs through the public batch entry point
+        (concurrent on the serving slots), or one design alone for B = 1."""
+        if len(batch) == 1:
+            C, st = shl.shl_homogenize(h, batch[0], r, opts, stream=stream)
+            return [C], [st]
+        C, st = shl.shl_homogenize_batch(h, batch, [r] * len(batch), opts, stream=stream)
+        return list(C), st
+
+    for k in range(args.warmup):
+        solve(batches[k])
     torch.cuda.synchronize()
     c0 = shl.shl_get_counters(h)["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -545,12 +567,12 @@ def main():
             stream.synchronize()
             t0 = time.perf_counter()
             ev[k][0].record(stream)
-            C, st = shl.shl_homogenize(h, designs[args.warmup + k], r, opts, stream=stream)
-            Cs.append(C)
+            C, st = solve(batches[args.warmup + k])
+            Cs += C
             ev[k][1].record(stream)
             stream.synchronize()
             wall.append(time.perf_counter() - t0)
-            stats.append(st)
+            stats += st
     torch.cuda.synchronize()
     c1 = shl.shl_get_counters(h)["kernel_launches"]
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
@@ -560,42 +582,65 @@ def main():
         t = torch.tensor([dev_s, wall_s], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_s, wall_s = float(t[0]), float(t[1])
-    value = world * args.steps / dev_s
-    e2e = world * args.steps / wall_s
+    value = world * args.steps * B / dev_s
+    e2e = world * args.steps * B / wall_s
+
+    # the same designs one at a time (single-design latency), a sample of them
+    seq = None
+    if B > 1:
+        n_seq = min(len(Cs), 8)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(n_seq):
+            shl.shl_homogenize(h, designs[args.warmup * B + i], r, opts, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_s = e0.elapsed_time(e1) / 1e3
+        seq = {"designs_per_s": n_seq / seq_s, "ms_per_design": 1e3 * seq_s / n_seq, "designs": n_seq}
 
     # dominant kernel: the FP32 stiffness apply of the inner solves, timed on
     # the launch stream on the last design's mask
     apply_s = time_apply(h, r, designs[-1], stream)
     roofline = apply_roofline(r, apply_s)
 
-    # accuracy of every timed design (untimed): C^H against the plain FP64 GPU
-    # path solved to 1e-11, entry error relative to max(|C_ij|, 1e-2 max|C|)
+    # accuracy of the timed designs (untimed): C^H against the plain FP64 GPU
+    # path solved to 1e-11, entry error relative to max(|C_ij|, 1e-2 max|C|);
+    # every design of the first timed batch and the first of each later one
     ref = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-11)
     acc = 0.0
-    for k in range(args.steps):
-        Cr, _ = shl.shl_homogenize(h, designs[args.warmup + k], r, ref, stream=stream)
-        acc = max(acc, float(np.max(np.abs(Cs[k] - Cr) / np.maximum(np.abs(Cr), 1e-2 * np.abs(Cr).max()))))
+    check = list(range(B)) + [k * B for k in range(1, args.steps)]
+    Crs, _ = shl.shl_homogenize_batch(h, [designs[args.warmup * B + i] for i in check], [r] * len(check), ref,
+                                      stream=stream)
+    for i, Cr in zip(check, Crs):
+        acc = max(acc, float(np.max(np.abs(Cs[i] - Cr) / np.maximum(np.abs(Cr), 1e-2 * np.abs(Cr).max()))))
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([acc], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         acc = float(t[0])
-    accuracy = {"chom_entry_err_max": acc, "bound": 1e-4, "designs": args.steps * world,
+    accuracy = {"chom_entry_err_max": acc, "bound": 1e-4, "designs": len(check) * world,
                 "reference": "FP64 GPU path, tol 1e-11"}
     if args.workload == "cubic128":
         accuracy["cubic_symmetry_err_max"] = max(cubic_symmetry_err(C) for C in Cs)
 
-    # the plain FP64 GPU path on the last design at the same tolerance (equal accuracy)
+    # the plain FP64 GPU path at the same tolerance (equal accuracy), in the
+    # same form: the first timed batch, concurrent on the same slots
     compare = None
     if not args.no_compare and prec == shl.SHL_FP32_REFINE and rank == 0:
         o64 = shl.default_solve_opts(precision=shl.SHL_FP64, tol=args.tol)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        first = batches[args.warmup]
         e0.record(stream)
-        C64, st64 = shl.shl_homogenize(h, designs[-1], r, o64, stream=stream)
+        if B == 1:
+            st64 = [shl.shl_homogenize(h, first[0], r, o64, stream=stream)[1]]
+        else:
+            st64 = shl.shl_homogenize_batch(h, first, [r] * B, o64, stream=stream)[1]
         e1.record(stream)
         torch.cuda.synchronize()
         s64 = e0.elapsed_time(e1) / 1e3
-        compare = {"fp64_designs_per_s": 1.0 / s64, "fp64_iters": max(st64["iters"]), "tol": args.tol}
+        compare = {"fp64_designs_per_s": B / s64, "fp64_iters_max": max(max(s["iters"]) for s in st64),
+                   "tol": args.tol, "designs": B}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -607,12 +652,12 @@ def main():
         line = {
             "metric": "homogenized designs/sec", "value": value, "unit": "designs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+            "designs_per_step": B, "sequential": seq,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": desc, "r": r, "precision": args.precision,
-                       "tol": args.tol, "l2": "flushed between steps", "parallelism": f"replicas x{world}"},
-            "e2e": {"value": e2e, "unit": "designs/s", "h2d_bytes_per_step": int(d0.pos.nbytes + d0.q.nbytes),
-                    "d2h_bytes_per_step": 36 * 8},
+            "config": bench_config(args, r, desc, world),
+            "e2e": {"value": e2e, "unit": "designs/s", "h2d_bytes_per_step": int(B * (d0.pos.nbytes + d0.q.nbytes)),
+                    "d2h_bytes_per_step": B * 36 * 8},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(c1 - c0),
             "solver": {"iters_max": [max(s["iters"]) for s in stats], "n_refine": [s["n_refine"] for s in stats],

@@ -258,7 +258,17 @@ int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts 
              double dE_dV, double *u_dev, double *C_out, double *g_pos, double *g_q, double *g_iso, double *g_t,
              double *g_alpha, double *V_out, shl_stats *st, void *stream);
 
-/* n designs, each on its own r[i]^3 grid; C_out: n x 36; st: n records or NULL. */
+/*
+ * n designs, each on its own r[i]^3 grid; C_out: n x 36; st: n records or
+ * NULL.  The designs run concurrently on the context's serving slots (up to
+ * max_batch at once, admitted by HBM footprint as in shl_serve_submit), each
+ * solved exactly as shl_homogenize would solve it alone.  Stream order: every
+ * design starts after the work queued on `stream` before the call, and work
+ * queued on `stream` after the call starts after every design.  Blocks until
+ * all are done.  SHL_EINVAL (nothing launched) if any design or the options
+ * are invalid or a footprint exceeds the budget; otherwise the first hard
+ * error of any design, else SHL_ENOCONV if any load case missed o->tol.
+ */
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
                          double *C_out, shl_stats *st, void *stream);
 

@@ -25,6 +25,13 @@
 namespace shl {
 
 // Device-resident scalars of one batched 6-RHS PCG solve.
+// Why a PCG case stopped with a numeric error (PcgState::numeric_err).
+constexpr int kNumErrPq = 1;       // p.q not positive or not finite (operator or direction)
+constexpr int kNumErrRz = 2;       // r.z not positive or not finite (preconditioner not SPD)
+constexpr int kNumErrResid = 3;    // recurrence r.z or r.r not finite
+constexpr int kNumErrInit = 4;     // initial residual not finite
+constexpr int kNumErrRestart = 5;  // true residual at a reliable update not finite
+
 struct PcgState {
     double rz[6];  // (r, z) of the current iterate
     double alpha[6], beta[6];
@@ -35,7 +42,7 @@ struct PcgState {
     int iters[6];
     int maxit;
     int nactive;
-    int numeric_err;
+    int numeric_err;  // 0, or the kNumErr* reason the last case stopped for
     unsigned ticket_apply, ticket_update, ticket_aux;
 };
 
@@ -368,7 +375,7 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
                 if (!a.st->active[kk]) continue;
                 const double pq = tot[kk];
                 if (!(pq > 0.0) || !isfinite(pq)) {
-                    a.st->numeric_err = 1;
+                    a.st->numeric_err = kNumErrPq;
                     a.st->active[kk] = 0;
                     a.st->alpha[kk] = 0.0;
                 } else {

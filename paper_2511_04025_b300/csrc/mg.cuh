@@ -143,7 +143,7 @@ __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, 
     }
 }
 
-__device__ inline void inv3(const double a[9], double o[9]) {
+__host__ __device__ inline void inv3(const double a[9], double o[9]) {
     const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
     const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
     const double id = det != 0.0 ? 1.0 / det : 0.0;
@@ -158,12 +158,70 @@ __device__ inline void inv3(const double a[9], double o[9]) {
     o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
 }
 
-// Block-Jacobi inverse of a stencil level (center block).
+// Regularisation of the coarsest operator: + kMgCoarseReg E A_hom, A_hom the
+// all-solid stiffness on the coarsest grid.  Above the FP32 rounding of the
+// Galerkin sums there (~1e-5 of the largest entries), far below the stiffness
+// of any load-bearing mode.
+constexpr double kMgCoarseReg = 1e-4;
+
+// Eigenvalue floor of the coarse block inverses, relative to the block's
+// largest |eigenvalue|: keeps D^-1 SPD after FP32 storage (condition <= 1e5).
+constexpr double kMgBlockFloor = 1e-5;
+
+// SPD inverse of a symmetric 3x3 block given with FP32 rounding.  The block
+// is symmetrised, diagonalised by cyclic Jacobi rotations, and its
+// eigenvalues are raised to kMgBlockFloor |lambda|_max before inverting: a
+// node tied to the solid along one direction only has a nearly singular
+// Galerkin block that FP32 rounding can make indefinite.  (LDL^T pivots are
+// no substitute: all three can clear the floor while the smallest eigenvalue
+// does not.)  A zero block gives a zero inverse.
+__host__ __device__ inline void spd_inv3(const double a_in[9], double o[9]) {
+    double A[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[i][j] = 0.5 * (a_in[3 * i + j] + a_in[3 * j + i]);
+    const double tr = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]) + fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 10; ++sweep) {
+        const double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        if (!(off > 1e-15 * tr)) break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            if (A[p][q] == 0.0) continue;
+            const double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+            for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, q)
+                const double akp = A[k][p], akq = A[k][q];
+                A[k][p] = c * akp - sn * akq;
+                A[k][q] = sn * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {  // A <- J^T A (rows p, q)
+                const double apk = A[p][k], aqk = A[q][k];
+                A[p][k] = c * apk - sn * aqk;
+                A[q][k] = sn * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {  // V <- V J
+                const double vkp = V[k][p], vkq = V[k][q];
+                V[k][p] = c * vkp - sn * vkq;
+                V[k][q] = sn * vkp + c * vkq;
+            }
+        }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < 3; ++i) lmax = fmax(lmax, fabs(A[i][i]));
+    double il[3];
+    for (int i = 0; i < 3; ++i) il[i] = lmax > 0.0 ? 1.0 / fmax(A[i][i], kMgBlockFloor * lmax) : 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            o[3 * i + j] = V[i][0] * il[0] * V[j][0] + V[i][1] * il[1] * V[j][1] + V[i][2] * il[2] * V[j][2];
+}
+
+// Block-Jacobi inverse of a stencil level (center block), SPD by construction.
 __global__ void mg_dinv_stencil_kernel(size_t N, const float *S, float *Dinv) {
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         double a[9], o[9];
         for (int m = 0; m < 9; ++m) a[m] = S[(n * 27 + 13) * 9 + m];
-        inv3(a, o);
+        spd_inv3(a, o);
         for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = (float)o[m];
     }
 }
@@ -488,25 +546,39 @@ __global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nr
         x[n] = y[n] * inv;
 }
 
-// x = Ainv b on the coarsest level (dense, 3N x 3N, applied per load case):
-// one warp per (load case, row), lanes split the columns (coalesced row of
-// Ainv), fixed shuffle tree.
-__global__ void mg_dense_solve_kernel(int n3, const float *__restrict__ Ainv, const float *__restrict__ b,
-                                      float *__restrict__ x, const PcgState *st) {
+// x = Y^T (Y b) on the coarsest level, Y = L^-1 the inverse Cholesky factor
+// of the pinned coarse operator (FP32, lower triangular, the rows and columns
+// of node 0 zero).  Y^T Y is positive semi-definite whatever the rounding of
+// Y, so the coarse correction cannot make the V-cycle indefinite (an explicit
+// FP32 inverse of a badly conditioned coarse operator can).  One block per
+// load case; w = Y b stays in shared memory; one warp per row, lanes split
+// the columns (coalesced rows of Y and of YT = Y^T), fixed shuffle tree.
+__global__ void mg_dense_solve_kernel(int n3, const float *__restrict__ Y, const float *__restrict__ YT,
+                                      const float *__restrict__ b, float *__restrict__ x, const PcgState *st) {
+    __shared__ float w[3 * kMgMaxCoarse];
     pdl_enter();
     if (mg_done(st)) return;
+    const int k = blockIdx.x;
+    if (st && !st->active[k]) return;  // block-uniform
     const int N = n3 / 3;
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < 6 * n3; wi += nw) {
-        const int k = wi / n3, row = wi - k * n3;
-        if (st && !st->active[k]) continue;  // warp-uniform
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float *bk = b + (size_t)3 * k * N;
+    for (int row = threadIdx.x >> 5; row < n3; row += nw) {
         float s = 0.0f;
-        for (int col = lane; col < n3; col += 32)
-            s += Ainv[(size_t)row * n3 + col] * b[(size_t)(3 * k + col % 3) * N + col / 3];
+        for (int col = lane; col <= row; col += 32) s += Y[(size_t)row * n3 + col] * bk[(size_t)(col % 3) * N + col / 3];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[(size_t)(3 * k + row % 3) * N + row / 3] = s;
+        if (lane == 0) w[row] = s;
+    }
+    __syncthreads();
+    float *xk = x + (size_t)3 * k * N;
+    for (int row = threadIdx.x >> 5; row < n3; row += nw) {
+        float s = 0.0f;
+        for (int col = (row & ~31) + lane; col < n3; col += 32)
+            if (col >= row) s += YT[(size_t)row * n3 + col] * w[col];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) xk[(size_t)(row % 3) * N + row / 3] = s;
     }
 }
 

@@ -74,7 +74,7 @@ __global__ void pcg_update_kernel(VecArgs<T> a) {
             const double rz = tot[k], rr = tot[6 + k];
             st->rr[k] = rr;
             if (!isfinite(rz) || !isfinite(rr)) {
-                st->numeric_err = 1;
+                st->numeric_err = kNumErrResid;
                 st->active[k] = 0;
             } else if (rr <= st->tol2 * st->bnorm2[k]) {
                 st->active[k] = 0;
@@ -122,7 +122,7 @@ __global__ void pcg_rz_kernel(VecArgs<T> a) {
         for (int k = 0; k < 6; ++k) {
             if (!act[k]) continue;
             if (!isfinite(tot[k]) || !(tot[k] > 0.0)) {
-                st->numeric_err = 1;
+                st->numeric_err = kNumErrRz;
                 st->active[k] = 0;
                 continue;
             }
@@ -240,7 +240,7 @@ __global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
             const bool want = (want_mask >> k) & 1;
             st->active[k] = want && (tot[6 + k] > st->tol2 * st->bnorm2[k]) && st->bnorm2[k] > 0.0;
             if (want && !isfinite(tot[6 + k])) {
-                st->numeric_err = 1;
+                st->numeric_err = kNumErrInit;
                 st->active[k] = 0;
             }
             na += st->active[k];
@@ -319,7 +319,7 @@ __global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, int 
                 st->rz[k] = tot[k];
                 st->rr[k] = tot[6 + k];
                 if (!isfinite(rr_true[k]) || !isfinite(tot[k])) {
-                    st->numeric_err = 1;
+                    st->numeric_err = kNumErrRestart;
                     st->active[k] = 0;
                 } else {
                     st->active[k] = (rr_true[k] > st->tol2 * st->bnorm2[k]) && (st->iters[k] < st->maxit);

@@ -29,6 +29,11 @@ struct ServeJob {
     size_t footprint = 0;
     bool done = false, running = false;
     shl_result res{};
+    // batch jobs: the slot's stream waits on `after` before the job's first
+    // launch and records `finished` after its last, so that the caller's
+    // stream can be ordered around work that ran on the slots' streams
+    cudaEvent_t after = nullptr, finished = nullptr;
+    std::string err;  // the slot's error text when the job failed
 };
 
 struct WarmEntry {
@@ -131,12 +136,16 @@ inline void serve_worker(Server *sv, int slot) {
                 warm = true;
             }
         }
+        if (rc == SHL_OK && job->after && cudaStreamWaitEvent(w->stream, job->after, 0) != cudaSuccess)
+            rc = set_err(w, SHL_ECUDA, "serving: stream wait failed");
         if (rc == SHL_OK) {
             std::lock_guard<std::recursive_mutex> wl(w->mu);
             rc = homogenize_impl(w, &d, r, &job->req.opts, job->res.C, &job->res.stats, w->stream, x64, warm);
         }
+        if (job->finished) cudaEventRecord(job->finished, w->stream);
         job->res.warm = warm ? 1 : 0;
         if (job->res.stats.status == SHL_OK && rc != SHL_OK) job->res.stats.status = rc;
+        if (rc != SHL_OK) job->err = w->err;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->slot_bytes[slot] = std::max(sv->slot_bytes[slot], ctx_ws_bytes(w));
@@ -243,13 +252,11 @@ inline void serve_stop(shl_ctx *ctx) {
 
 }  // namespace shl
 
-extern "C" {
+namespace shl {
 
-int shl_serve_submit(shl_ctx *ctx, const shl_request *req, uint64_t *ticket) {
-    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
-    if (!req || !ticket) return set_err(ctx, SHL_EINVAL, "serving: NULL request or ticket");
-    SHL_TRY(validate_solve_opts(ctx, &req->opts));
-    SHL_TRY(validate_design(ctx, &req->design, req->r));
+// Queue one validated request on the context's server (started on first use).
+inline int serve_enqueue(shl_ctx *ctx, const shl_request *req, cudaEvent_t after, cudaEvent_t finished,
+                         uint64_t *ticket) {
     cudaSetDevice(ctx->device);
     Server *sv = nullptr;
     {
@@ -257,6 +264,8 @@ int shl_serve_submit(shl_ctx *ctx, const shl_request *req, uint64_t *ticket) {
         SHL_TRY(serve_start(ctx, &sv));
     }
     auto job = std::make_unique<ServeJob>();
+    job->after = after;
+    job->finished = finished;
     job->req = *req;
     const int n = req->design.n, K = req->design.K;
     job->pos.assign(req->design.pos, req->design.pos + 3 * n);
@@ -277,6 +286,18 @@ int shl_serve_submit(shl_ctx *ctx, const shl_request *req, uint64_t *ticket) {
     return SHL_OK;
 }
 
+}  // namespace shl
+
+extern "C" {
+
+int shl_serve_submit(shl_ctx *ctx, const shl_request *req, uint64_t *ticket) {
+    if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
+    if (!req || !ticket) return set_err(ctx, SHL_EINVAL, "serving: NULL request or ticket");
+    SHL_TRY(validate_solve_opts(ctx, &req->opts));
+    SHL_TRY(validate_design(ctx, &req->design, req->r));
+    return serve_enqueue(ctx, req, nullptr, nullptr, ticket);
+}
+
 static int serve_take(shl_ctx *ctx, uint64_t ticket, shl_result *out, bool block) {
     if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
     auto *sv = static_cast<Server *>(ctx->serve);
@@ -290,6 +311,7 @@ static int serve_take(shl_ctx *ctx, uint64_t ticket, shl_result *out, bool block
         sv->cv_done.wait(lk, [&] { return j->done; });
     }
     if (out) *out = it->second->res;
+    if (!it->second->err.empty()) ctx->err = it->second->err;  // why the request failed
     sv->jobs.erase(it);
     return SHL_OK;
 }

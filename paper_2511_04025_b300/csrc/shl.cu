@@ -340,6 +340,17 @@ ApplyArgs<T> make_apply(int r, const Density &den, const ElemOp<T> &op) {
 
 // One PCG iteration recorded as a CUDA graph and replayed: the V-cycle alone
 // is ~40 small kernels, whose host launch cost would otherwise dominate.
+inline const char *numeric_err_text(int code) {
+    switch (code) {
+        case kNumErrPq: return "p.q not positive or not finite";
+        case kNumErrRz: return "r.z not positive or not finite (preconditioner not SPD)";
+        case kNumErrResid: return "recurrence residual not finite";
+        case kNumErrInit: return "initial residual not finite";
+        case kNumErrRestart: return "true residual at a reliable update not finite";
+        default: return "numeric error";
+    }
+}
+
 struct IterGraph {
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches = 0;  // kernels per replay
@@ -551,7 +562,7 @@ struct MgLevel {
 struct Mg {
     int L = 0;  // coarsest level index
     MgLevel lv[kMgMaxLevels];
-    float *Ainv = nullptr;  // coarsest dense inverse
+    float *Y = nullptr, *YT = nullptr;  // coarsest: inverse Cholesky factor and its transpose
     int n3 = 0;
     int nu = 2;
 };
@@ -692,14 +703,52 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     A[(3 * (I - 1) + i) * (size_t)m + 3 * (J - 1) + j] += Sh[(I * 27 + dl) * 9 + 3 * i + j];
         }
     }
+    // + eps E A_hom: the all-solid stiffness of the coarsest grid, h_c Khat per
+    // element (the Galerkin product of a uniform fine mesh, exact for
+    // trilinear elements).  A piece of solid held only by the ersatz void has
+    // a mechanism whose stiffness here (~E_void) is below the FP32 rounding of
+    // the Galerkin sums; unregularised, the coarse solve amplifies it by ~1e15
+    // and CG loses the sign of r.z.  The shift lifts such modes in proportion
+    // to their geometric stiffness and leaves the pinned translations alone.
+    {
+        double Ku[24][24];
+        unit_hex8_stiffness(o->nu, Ku);
+        const double w = kMgCoarseReg * o->E / rc;
+        for (int ez = 0; ez < rc; ++ez)
+            for (int ey = 0; ey < rc; ++ey)
+                for (int ex = 0; ex < rc; ++ex) {
+                    int nd[8];
+                    for (int b = 0; b < 8; ++b)
+                        nd[b] = ((ez + ((b >> 2) & 1)) % rc * rc + (ey + ((b >> 1) & 1)) % rc) * rc + (ex + (b & 1)) % rc;
+                    for (int a = 0; a < 8; ++a) {
+                        if (nd[a] == 0) continue;
+                        for (int b = 0; b < 8; ++b) {
+                            if (nd[b] == 0) continue;
+                            for (int i = 0; i < 3; ++i)
+                                for (int j = 0; j < 3; ++j)
+                                    A[(size_t)(3 * (nd[a] - 1) + i) * m + 3 * (nd[b] - 1) + j] +=
+                                        w * Ku[3 * a + i][3 * b + j];
+                        }
+                    }
+                }
+    }
     // symmetrise (FP32 stencil rounding), Cholesky, explicit inverse
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < i; ++j) A[(size_t)i * m + j] = A[(size_t)j * m + i] = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
+    // A pivot at or below the FP32 rounding level of the stencil sums (a
+    // near-rigid mode of a nearly void coarse cell) is raised to that level:
+    // L L^T stays SPD whenever L has a positive diagonal, which is all the
+    // preconditioner needs.
+    double dmax = 0.0;
+    for (int j = 0; j < m; ++j) dmax = std::max(dmax, std::fabs(A[(size_t)j * m + j]));
     std::vector<double> Lc((size_t)m * m, 0.0);
     for (int j = 0; j < m; ++j) {
         double d = A[(size_t)j * m + j];
+        const double floor_j = 1e-7 * std::max(std::fabs(d), 1e-6 * dmax);
         for (int k = 0; k < j; ++k) d -= Lc[(size_t)j * m + k] * Lc[(size_t)j * m + k];
-        if (!(d > 0.0)) return set_err(ctx, SHL_ENUMERIC, "coarsest multigrid operator is not positive definite");
+        if (!std::isfinite(d) || !(floor_j > 0.0))
+            return set_err(ctx, SHL_ENUMERIC, "coarsest multigrid operator is not finite");
+        if (!(d > floor_j)) d = floor_j;
         const double ljj = std::sqrt(d);
         Lc[(size_t)j * m + j] = ljj;
         for (int i = j + 1; i < m; ++i) {
@@ -708,8 +757,9 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             Lc[(size_t)i * m + j] = v / ljj;
         }
     }
-    // A^-1 = L^-T L^-1: Y = L^-1 (lower triangular) by row operations, then
-    // A^-1 = Y^T Y accumulated row by row (unit-stride inner loops throughout)
+    // A^-1 = L^-T L^-1 with Y = L^-1 (lower triangular) by row operations;
+    // the V-cycle applies Y^T (Y b), stored in FP32 with node 0's rows and
+    // columns zero, plus Y^T row-major for coalesced reads
     std::vector<double> Y((size_t)m * m, 0.0);
     for (int i = 0; i < m; ++i) {  // row i of L Y = I: Y[i][:i+1] = (e_i - sum_k<i L[i][k] Y[k]) / L[i][i]
         double *yi = &Y[(size_t)i * m];
@@ -722,24 +772,17 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         const double inv = 1.0 / Lc[(size_t)i * m + i];
         for (int c = 0; c <= i; ++c) yi[c] *= inv;
     }
-    std::vector<double> G((size_t)m * m, 0.0);  // lower triangle of Y^T Y
-    for (int i = 0; i < m; ++i) {
-        const double *yi = &Y[(size_t)i * m];
-        for (int a = 0; a <= i; ++a) {
-            const double ya = yi[a];
-            double *ga = &G[(size_t)a * m];
-            for (int b = 0; b <= a; ++b) ga[b] += ya * yi[b];
-        }
-    }
-    std::vector<float> Ainv((size_t)n3 * n3, 0.0f);
+    std::vector<float> Yf((size_t)2 * n3 * n3, 0.0f);
+    float *YTf = Yf.data() + (size_t)n3 * n3;
     for (int a = 0; a < m; ++a)
-        for (int b = 0; b <= a; ++b) {
-            const float v = (float)G[(size_t)a * m + b];
-            Ainv[(size_t)(a + 3) * n3 + (b + 3)] = v;
-            Ainv[(size_t)(b + 3) * n3 + (a + 3)] = v;
+        for (int c = 0; c <= a; ++c) {
+            const float v = (float)Y[(size_t)a * m + c];
+            Yf[(size_t)(a + 3) * n3 + (c + 3)] = v;
+            YTf[(size_t)(c + 3) * n3 + (a + 3)] = v;
         }
-    SHL_TRY(ws_get_t(ctx, "mg_Ainv", (size_t)n3 * n3, &mg->Ainv));
-    SHL_CUDA(ctx, cudaMemcpyAsync(mg->Ainv, Ainv.data(), Ainv.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    SHL_TRY(ws_get_t(ctx, "mg_Y", (size_t)2 * n3 * n3, &mg->Y));
+    mg->YT = mg->Y + (size_t)n3 * n3;
+    SHL_CUDA(ctx, cudaMemcpyAsync(mg->Y, Yf.data(), Yf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
     return SHL_OK;
 }
@@ -800,8 +843,8 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     }
     {
         MgLevel &C = mg->lv[mg->L];
-        pdl_launch(mg_dense_solve_kernel, grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4), kBlk, 0, s, mg->n3,
-                   mg->Ainv, C.b, C.x, st);
+        pdl_launch(mg_dense_solve_kernel, 6, 1024, 0, s, mg->n3, (const float *)mg->Y, (const float *)mg->YT, C.b,
+                   C.x, st);
         ++ctx->launches;
     }
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
@@ -874,6 +917,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                 if ((want >> k) & 1) total_it[k] += its[k];
             if (nerr) {
                 out->status = SHL_ENUMERIC;
+                set_err(ctx, SHL_ENUMERIC, "FP64 PCG stopped: %s", numeric_err_text(nerr));
                 break;
             }
             want = 0;
@@ -979,6 +1023,11 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                 SHL_CUDA(ctx, cudaStreamSynchronize(s));
                 if (hst.numeric_err) {
                     out->status = SHL_ENUMERIC;
+                    int itmax = 0;
+                    for (int k = 0; k < 6; ++k) itmax = std::max(itmax, hst.iters[k]);
+                    set_err(ctx, SHL_ENUMERIC, "%s PCG stopped at iteration %d: %s",
+                            use_mg ? "multigrid-preconditioned" : "Jacobi-preconditioned", itmax,
+                            numeric_err_text(hst.numeric_err));
                     break;
                 }
                 // want: load cases not yet verified converged by their FP64 residual
@@ -1097,8 +1146,10 @@ inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double
     cudaEventCreate(&e2);
     cudaEventRecord(e0, s);
     int rc = run_solve(ctx, r, den, o, x64, warm, s, &so);
-    if (rc == SHL_OK && so.status == SHL_ENUMERIC && so.precond == SHL_PRECOND_MG) {
-        // multigrid-preconditioned CG broke down: solve again with point Jacobi
+    if ((rc == SHL_OK && so.status == SHL_ENUMERIC && so.precond == SHL_PRECOND_MG) ||
+        (rc == SHL_ENUMERIC && o->precond == SHL_PRECOND_MG)) {
+        // multigrid setup or the multigrid-preconditioned CG broke down:
+        // solve again with point Jacobi
         shl_solve_opts oj = *o;
         oj.precond = SHL_PRECOND_JACOBI;
         so = SolveOut();
@@ -1126,7 +1177,7 @@ inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
     if (rc != SHL_OK) return rc;
-    if (so.status == SHL_ENUMERIC) return set_err(ctx, SHL_ENUMERIC, "NaN/Inf in the solve");
+    if (so.status == SHL_ENUMERIC) return set_err(ctx, SHL_ENUMERIC, "solve broke down: %s", ctx->err.c_str());
     if (so.status == SHL_ENOCONV) return set_err(ctx, SHL_ENOCONV, "a load case did not reach tol");
     return SHL_OK;
 }
@@ -1481,17 +1532,68 @@ int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts 
                      pick_stream(ctx, stream));
 }
 
+// The designs of a batch run concurrently on the serving slots (each a
+// private context with its own stream and workspaces), so that one design's
+// latency-bound phases (small coarse-grid kernels, host reads of convergence
+// flags) overlap with the others' bandwidth-bound applies.
 int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int32_t *r, const shl_solve_opts *o,
                          double *C_out, shl_stats *st, void *stream) {
     if (!ctx) return set_err(nullptr, SHL_EINVAL, "ctx is NULL");
     if (n < 0 || (n > 0 && (!d || !r || !C_out))) return set_err(ctx, SHL_EINVAL, "bad batch arguments");
-    int worst = SHL_OK;
-    for (int i = 0; i < n; ++i) {
-        int rc = shl_homogenize(ctx, d + i, r[i], o, C_out + 36 * i, st ? st + i : nullptr, stream);
-        if (rc != SHL_OK && rc != SHL_ENOCONV) return rc;
-        if (rc != SHL_OK) worst = rc;
+    if (n == 0) return SHL_OK;
+    SHL_TRY(validate_solve_opts(ctx, o));
+    for (int i = 0; i < n; ++i) SHL_TRY(validate_design(ctx, d + i, r[i]));
+    if (n == 1) return shl_homogenize(ctx, d, r[0], o, C_out, st, stream);
+    cudaSetDevice(ctx->device);
+    cudaStream_t cs = pick_stream(ctx, stream);
+    Server *sv = nullptr;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        SHL_TRY(serve_start(ctx, &sv));
     }
-    return worst;
+    for (int i = 0; i < n; ++i)
+        if (design_footprint(r[i], o) > sv->budget)
+            return set_err(ctx, SHL_EINVAL, "batch: design %d footprint exceeds the HBM budget %zu", i, sv->budget);
+    cudaEvent_t entry = nullptr;
+    SHL_CUDA(ctx, cudaEventCreateWithFlags(&entry, cudaEventDisableTiming));
+    std::vector<cudaEvent_t> fin(n, nullptr);
+    std::vector<uint64_t> tk(n, 0);
+    int err = cudaEventRecord(entry, cs) == cudaSuccess ? SHL_OK : set_err(ctx, SHL_ECUDA, "batch: event record failed");
+    int submitted = 0;
+    for (int i = 0; i < n && err == SHL_OK; ++i) {
+        if (cudaEventCreateWithFlags(&fin[i], cudaEventDisableTiming) != cudaSuccess) {
+            err = set_err(ctx, SHL_ECUDA, "batch: event create failed");
+            break;
+        }
+        shl_request req{};
+        req.design = d[i];
+        req.r = r[i];
+        req.opts = *o;
+        req.session = -1;
+        err = serve_enqueue(ctx, &req, entry, fin[i], &tk[i]);
+        if (err == SHL_OK) ++submitted;
+    }
+    int worst = SHL_OK;
+    for (int i = 0; i < submitted; ++i) {
+        shl_result res{};
+        const int rc = serve_take(ctx, tk[i], &res, true);
+        if (rc != SHL_OK) {
+            if (err == SHL_OK) err = rc;
+            continue;
+        }
+        std::memcpy(C_out + 36 * i, res.C, sizeof(res.C));
+        if (st) st[i] = res.stats;
+        const int s = res.stats.status;
+        if (s == SHL_ENOCONV && worst == SHL_OK) worst = s;
+        if (s != SHL_OK && s != SHL_ENOCONV && err == SHL_OK)
+            err = set_err(ctx, s, "batch: design %d failed: %s", i, ctx->err.c_str());
+        if (cudaStreamWaitEvent(cs, fin[i], 0) != cudaSuccess && err == SHL_OK)
+            err = set_err(ctx, SHL_ECUDA, "batch: stream wait failed");
+    }
+    for (auto e : fin)
+        if (e) cudaEventDestroy(e);
+    cudaEventDestroy(entry);
+    return err != SHL_OK ? err : worst;
 }
 
 int shl_get_counters(shl_ctx *ctx, shl_counters *out) {

@@ -173,7 +173,7 @@ __global__ void pcg_alpha_kernel(PcgState *st, ApplyDot ad) {
             if (act) {
                 const double p = pick6(pq, 0, k);
                 if (!(p > 0.0) || !isfinite(p)) {
-                    st->numeric_err = 1;
+                    st->numeric_err = kNumErrPq;
                     st->alpha[k] = 0.0;
                     act = 0;
                     st->active[k] = 0;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kerne
                 const double rz = pick6(tot, 0, kk), rr = pick6(tot, 6, kk);
                 st->rr[kk] = rr;
                 if (!isfinite(rz) || !isfinite(rr)) {
-                    st->numeric_err = 1;
+                    st->numeric_err = kNumErrResid;
                     act = 0;
                 } else if (rr <= st->tol2 * st->bnorm2[kk]) {
                     act = 0;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_jacobi_rz_ke
             if (act) {
                 const double rz = pick6(tot, 0, kk);
                 if (!isfinite(rz) || !(rz > 0.0)) {
-                    st->numeric_err = 1;
+                    st->numeric_err = kNumErrRz;
                     act = 0;
                     st->active[kk] = 0;
                 } else {
