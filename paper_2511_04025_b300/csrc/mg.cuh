@@ -550,35 +550,45 @@ __global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nr
 // of the pinned coarse operator (FP32, lower triangular, the rows and columns
 // of node 0 zero).  Y^T Y is positive semi-definite whatever the rounding of
 // Y, so the coarse correction cannot make the V-cycle indefinite (an explicit
-// FP32 inverse of a badly conditioned coarse operator can).  One block per
-// load case; w = Y b stays in shared memory; one warp per row, lanes split
-// the columns (coalesced rows of Y and of YT = Y^T), fixed shuffle tree.
-__global__ void mg_dense_solve_kernel(int n3, const float *__restrict__ Y, const float *__restrict__ YT,
-                                      const float *__restrict__ b, float *__restrict__ x, const PcgState *st) {
-    __shared__ float w[3 * kMgMaxCoarse];
+// FP32 inverse of a badly conditioned coarse operator can).  Two launches,
+// w = Y b then x = Y^T w (YT = Y^T row-major), each one warp per (load case,
+// row), lanes split the columns of a coalesced row, fixed shuffle tree.
+__global__ void mg_dense_y_kernel(int n3, const float *__restrict__ Y, const float *__restrict__ b,
+                                  float *__restrict__ w, const PcgState *st) {
     pdl_enter();
     if (mg_done(st)) return;
-    const int k = blockIdx.x;
-    if (st && !st->active[k]) return;  // block-uniform
     const int N = n3 / 3;
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const float *bk = b + (size_t)3 * k * N;
-    for (int row = threadIdx.x >> 5; row < n3; row += nw) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < 6 * n3; wi += nw) {
+        const int k = wi / n3, row = wi - k * n3;
+        if (st && !st->active[k]) continue;  // warp-uniform
+        const float *bk = b + (size_t)3 * k * N;
         float s = 0.0f;
         for (int col = lane; col <= row; col += 32) s += Y[(size_t)row * n3 + col] * bk[(size_t)(col % 3) * N + col / 3];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) w[row] = s;
+        if (lane == 0) w[wi] = s;
     }
-    __syncthreads();
-    float *xk = x + (size_t)3 * k * N;
-    for (int row = threadIdx.x >> 5; row < n3; row += nw) {
+}
+
+__global__ void mg_dense_yt_kernel(int n3, const float *__restrict__ YT, const float *__restrict__ w,
+                                   float *__restrict__ x, const PcgState *st) {
+    pdl_enter();
+    if (mg_done(st)) return;
+    const int N = n3 / 3;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < 6 * n3; wi += nw) {
+        const int k = wi / n3, row = wi - k * n3;
+        if (st && !st->active[k]) continue;  // warp-uniform
+        const float *wk = w + (size_t)k * n3;
         float s = 0.0f;
         for (int col = (row & ~31) + lane; col < n3; col += 32)
-            if (col >= row) s += YT[(size_t)row * n3 + col] * w[col];
+            if (col >= row) s += YT[(size_t)row * n3 + col] * wk[col];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) xk[(size_t)(row % 3) * N + row / 3] = s;
+        if (lane == 0) x[(size_t)(3 * k + row % 3) * N + row / 3] = s;
     }
 }
 

@@ -563,6 +563,7 @@ struct Mg {
     int L = 0;  // coarsest level index
     MgLevel lv[kMgMaxLevels];
     float *Y = nullptr, *YT = nullptr;  // coarsest: inverse Cholesky factor and its transpose
+    float *w = nullptr;                 // coarsest: Y b, 6 x n3
     int n3 = 0;
     int nu = 2;
 };
@@ -780,8 +781,9 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             Yf[(size_t)(a + 3) * n3 + (c + 3)] = v;
             YTf[(size_t)(c + 3) * n3 + (a + 3)] = v;
         }
-    SHL_TRY(ws_get_t(ctx, "mg_Y", (size_t)2 * n3 * n3, &mg->Y));
+    SHL_TRY(ws_get_t(ctx, "mg_Y", (size_t)2 * n3 * n3 + (size_t)6 * n3, &mg->Y));
     mg->YT = mg->Y + (size_t)n3 * n3;
+    mg->w = mg->YT + (size_t)n3 * n3;
     SHL_CUDA(ctx, cudaMemcpyAsync(mg->Y, Yf.data(), Yf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
     return SHL_OK;
@@ -843,9 +845,10 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     }
     {
         MgLevel &C = mg->lv[mg->L];
-        pdl_launch(mg_dense_solve_kernel, 6, 1024, 0, s, mg->n3, (const float *)mg->Y, (const float *)mg->YT, C.b,
-                   C.x, st);
-        ++ctx->launches;
+        const int g = grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4);
+        pdl_launch(mg_dense_y_kernel, g, kBlk, 0, s, mg->n3, (const float *)mg->Y, (const float *)C.b, mg->w, st);
+        pdl_launch(mg_dense_yt_kernel, g, kBlk, 0, s, mg->n3, (const float *)mg->YT, (const float *)mg->w, C.x, st);
+        ctx->launches += 2;
     }
     for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
         MgLevel &L = mg->lv[l];

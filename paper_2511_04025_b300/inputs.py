@@ -127,6 +127,15 @@ def gradient_64(seed: int = 0) -> Design:
     return Design(pos=pos, q=_balanced_signs(24), iso=0.0, vf=0.10)
 
 
+def shell_256(seed: int = 0) -> Design:
+    """256^3 thin shell in the setting of the paper's timing table (Sec. 5.4):
+    explicit half-thickness t = 0.02 (cell units), 32 charges balanced +-1
+    uniform in the cell (about 9-10 % solid)."""
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0.0, 1.0, size=(32, 3))
+    return Design(pos=pos, q=_balanced_signs(32), iso=0.0, t=0.02)
+
+
 def random_design(seed: int, n: int, vf: float, balanced: bool = True) -> Design:
     rng = np.random.default_rng(seed)
     pos = rng.uniform(0.0, 1.0, size=(n, 3))
