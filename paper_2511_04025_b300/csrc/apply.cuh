@@ -108,7 +108,11 @@ __host__ __device__ inline int wrap_near(int v, int r) { return v < 0 ? v + r : 
 // bottom/top faces, add the bottom face to the carried top face of the
 // element below, untransform and hand the three foreign corners of the node
 // plane to the +x / +y / +xy neighbours.
-template <typename T, int TX, int TY, bool RESID>
+// SMOOTH selects the density at compile time (a.rho, else a.mask): the
+// smoothed modulus is formed in FP64 from rho, and a run-time branch lets the
+// compiler issue those FP64 instructions, predicated off, on every z step of
+// the binary-mask path too (B300's FP64 pipe is narrow).
+template <typename T, int TX, int TY, bool RESID, bool SMOOTH>
 __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4 ? 2 : 1)
     apply_kernel(const ApplyArgs<T> a) {
     pdl_enter();
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         const int exl = el ? tid % EX : 0, eyl = el ? tid / EX : 0;
         const int tiles_x = (r + TX - 1) / TX;
         const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
-        const int z0 = (int)(((long long)blockIdx.y * r) / a.zc), tz = (int)(((long long)(blockIdx.y + 1) * r) / a.zc) - z0;
+        const int z0 = (int)(blockIdx.y * r) / a.zc, tz = (int)((blockIdx.y + 1) * r) / a.zc - z0;
         const int ex = wrapi(x0 - 1 + exl, r), ey = wrapi(y0 - 1 + eyl, r);
         const int nx = x0 - 1 + exl, ny = y0 - 1 + eyl;
         const bool out_col = el && exl >= 1 && eyl >= 1 && nx < r && ny < r;
@@ -252,7 +256,11 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         auto modulus = [&](int ez) -> T {
             if (!el) return T(0);
             const size_t e = (size_t)(ez < 0 ? ez + r : (ez >= r ? ez - r : ez)) * rr + exy;
-            T Ee = a.rho ? (T)(a.Evoid + a.rho[e] * (a.E - a.Evoid)) : (a.mask[e] ? a.E : a.Evoid);
+            T Ee;
+            if constexpr (SMOOTH)
+                Ee = (T)(a.Evoid + a.rho[e] * (a.E - a.Evoid));
+            else
+                Ee = a.mask[e] ? a.E : a.Evoid;
             return RESID ? -Ee : Ee;
         };
 

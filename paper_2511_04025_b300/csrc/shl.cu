@@ -36,10 +36,11 @@ void apply_smem_attr() {
     cudaGetDevice(&dev);
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load(std::memory_order_acquire) & bit) return;
-    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ApplyShape<T, kTX, kTY>::smem());
-    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ApplyShape<T, kTX, kTY>::smem());
+    const int sm = (int)ApplyShape<T, kTX, kTY>::smem();
+    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(apply_kernel<T, kTX, kTY, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     done.fetch_or(bit, std::memory_order_release);
 }
 
@@ -125,10 +126,17 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
             a.ticket = ticket;
         }
     }
-    if (a.resid)
-        pdl_launch(apply_kernel<T, kTX, kTY, true>, g, S::THREADS, S::smem(), s, a);
-    else
-        pdl_launch(apply_kernel<T, kTX, kTY, false>, g, S::THREADS, S::smem(), s, a);
+    if (a.rho) {
+        if (a.resid)
+            pdl_launch(apply_kernel<T, kTX, kTY, true, true>, g, S::THREADS, S::smem(), s, a);
+        else
+            pdl_launch(apply_kernel<T, kTX, kTY, false, true>, g, S::THREADS, S::smem(), s, a);
+    } else {
+        if (a.resid)
+            pdl_launch(apply_kernel<T, kTX, kTY, true, false>, g, S::THREADS, S::smem(), s, a);
+        else
+            pdl_launch(apply_kernel<T, kTX, kTY, false, false>, g, S::THREADS, S::smem(), s, a);
+    }
     ++ctx->launches;
     SHL_CUDA(ctx, cudaGetLastError());
     return SHL_OK;
