@@ -365,11 +365,19 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
     if (!a.dot) return;
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    double dcase[6];
-    const double mine = dacc.get();
+    // the CTA's row: its own case's sum in column k, zeros elsewhere
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 v[1] = {dacc.get_df()};
+        double sum[1];
+        block_sum_df<1>(v, sum);
+        if (threadIdx.x < 6) a.partial[(size_t)bid * 6 + threadIdx.x] = threadIdx.x == (unsigned)k ? sum[0] : 0.0;
+    } else {
+        double dcase[6];
+        const double mine = dacc.get();
 #pragma unroll
-    for (int kk = 0; kk < 6; ++kk) dcase[kk] = (kk == k) ? mine : 0.0;
-    block_reduce_store<6>(dcase, a.partial, bid);
+        for (int kk = 0; kk < 6; ++kk) dcase[kk] = (kk == k) ? mine : 0.0;
+        block_reduce_store<6>(dcase, a.partial, bid);
+    }
     if (a.defer) return;  // the consumer reduces the per-CTA partials itself
     if (!last_block_ticket(a.ticket, nblocks)) return;
     __shared__ double tot[6];

@@ -190,6 +190,50 @@ __device__ inline void block_reduce_store(double (&v)[NV], double *partial, int 
     }
 }
 
+// Double-float arithmetic (a value carried as hi + lo in two floats) by
+// error-free transformations: Knuth's TwoSum gives s + e = a + b exactly.
+// Used where FP32 kernels combine compensated partial sums across a block:
+// B300's FP64 pipe is very narrow (one FP64 warp instruction occupies it for
+// ~16 cycles), so an FP64 shuffle tree in every block, or every thread
+// recomputing the same FP64 totals, costs microseconds at a kernel's tail.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+    const float2 t = two_sum(x.x, y.x);
+    const float lo = t.y + (x.y + y.y);
+    const float hi = t.x + lo;
+    return make_float2(hi, lo - (hi - t.x));
+}
+
+// Block sums of NV double-float values, returned in FP64 to every thread
+// (fixed order: xor shuffle tree, then warps in order; one FP64 add per value).
+template <int NV>
+__device__ inline void block_sum_df(const float2 (&v)[NV], double (&out)[NV]) {
+    __shared__ float2 red[NV][32];
+    __shared__ double res[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float2 s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s = df_add(s, make_float2(__shfl_xor_sync(0xffffffffu, s.x, o), __shfl_xor_sync(0xffffffffu, s.y, o)));
+        if (lane == 0) red[k][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float2 s = red[threadIdx.x][0];
+        for (int w = 1; w < nwarps; ++w) s = df_add(s, red[threadIdx.x][w]);
+        res[threadIdx.x] = (double)s.x + (double)s.y;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = res[k];
+}
+
 // Per-thread dot-product accumulator.  FP64 vectors accumulate in FP64.  FP32
 // vectors accumulate each thread's few products with compensated (Kahan)
 // FP32 summation and hand the result to the FP64 block/grid reduction: the
@@ -213,6 +257,7 @@ struct DotAcc<float> {
         s = t;
     }
     __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+    __device__ __forceinline__ float2 get_df() const { return two_sum(s, -c); }  // hi + lo = s - c exactly
 };
 
 // Returns true in every thread of the block that finished last.  Resets the

@@ -78,41 +78,40 @@ __device__ __forceinline__ void stc(T *p, const Chunk<T, V> &c) {
     }
 }
 
-// Last block: tot[v * 6 + k] = sum over the bpk blocks of case k of
-// partial[(k * bpk + j) * 2 + v], in a fixed order.
-__device__ inline void sum_case_partials(const double *partial, int bpk, double (&tot)[12]) {
-    __shared__ double red[12][32];
-    double s[12];
+// Last block, warp 0 only (the caller's other warps have left): tot[v * 6 + k]
+// = sum over the bpk blocks of case k of partial[(k * bpk + j) * 2 + v], in a
+// fixed order, the same in every lane.  One warp: the FP64 adds are few
+// (bpk / 32 per lane and value, then the shuffle tree), which matters on
+// B300's narrow FP64 pipe.
+__device__ inline void sum_case_partials_warp(const double *partial, int bpk, double (&tot)[12]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int m = 0; m < 12; ++m) s[m] = 0.0;
-    for (int j = threadIdx.x; j < bpk; j += blockDim.x)
+    for (int m = 0; m < 12; ++m) tot[m] = 0.0;
+    for (int j = lane; j < bpk; j += 32)
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            s[k] += __ldcg(partial + ((size_t)k * bpk + j) * 2 + 0);
-            s[6 + k] += __ldcg(partial + ((size_t)k * bpk + j) * 2 + 1);
+            tot[k] += __ldcg(partial + ((size_t)k * bpk + j) * 2 + 0);
+            tot[6 + k] += __ldcg(partial + ((size_t)k * bpk + j) * 2 + 1);
         }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int m = 0; m < 12; ++m) {
-        double x = s[m];
+    for (int m = 0; m < 12; ++m)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[m][warp] = x;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < 12; ++m) {
-        double x = 0.0;
-        for (int w = 0; w < nw; ++w) x += red[m][w];
-        tot[m] = x;
-    }
+        for (int o = 16; o > 0; o >>= 1) tot[m] += __shfl_xor_sync(0xffffffffu, tot[m], o);
 }
 
-// Block partials (d0, d1) -> partial[blockIdx.x * 2 + {0, 1}].
+// Block partials (d0, d1) -> partial[blockIdx.x * 2 + {0, 1}].  FP32
+// accumulators are combined as double-floats (no FP64 shuffle tree).
 template <typename T>
 __device__ inline void store_block_pair(const DotAcc<T> &d0, const DotAcc<T> &d1, double *partial) {
-    double v[2] = {d0.get(), d1.get()};
-    block_reduce_store<2>(v, partial, blockIdx.x);
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 v[2] = {d0.get_df(), d1.get_df()};
+        double s[2];
+        block_sum_df<2>(v, s);
+        if (threadIdx.x < 2) partial[(size_t)blockIdx.x * 2 + threadIdx.x] = s[threadIdx.x];
+    } else {
+        double v[2] = {d0.get(), d1.get()};
+        block_reduce_store<2>(v, partial, blockIdx.x);
+    }
 }
 
 // v[off + k] for a run-time k < 6 without local-memory indexing.
@@ -132,28 +131,19 @@ struct ApplyDot {
     int per_case;
 };
 
-// (p.q)_k of all six load cases at once (one pass over the partials, one
-// block reduction), the same values in every thread, fixed order.
-__device__ inline void case_pq_all(const ApplyDot &ad, double (&pq)[6]) {
-    __shared__ double red[6][32];
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < ad.per_case; b += blockDim.x)
+// (p.q)_k of all six load cases at once, warp 0 only (one pass over the
+// partials, one shuffle tree), the same values in every lane, fixed order.
+__device__ inline void case_pq_warp(const ApplyDot &ad, double (&pq)[6]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] += __ldcg(ad.partial + ((size_t)k * ad.per_case + b) * 6 + k);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < 6; ++k) pq[k] = 0.0;
+    for (int b = lane; b < ad.per_case; b += 32)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 6; ++k) pq[k] += __ldcg(ad.partial + ((size_t)k * ad.per_case + b) * 6 + k);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-        if (lane == 0) red[k][warp] = v[k];
-    }
-    __syncthreads();
+    for (int k = 0; k < 6; ++k)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += red[k][w];
-        pq[k] = t;
-    }
+        for (int o = 16; o > 0; o >>= 1) pq[k] += __shfl_xor_sync(0xffffffffu, pq[k], o);
 }
 
 // One block: alpha_k = rz_k / (p.q)_k for the active load cases, from the
@@ -161,9 +151,9 @@ __device__ inline void case_pq_all(const ApplyDot &ad, double (&pq)[6]) {
 // p.q stops the case with a numeric error.
 __global__ void pcg_alpha_kernel(PcgState *st, ApplyDot ad) {
     pdl_enter();
-    if (st->nactive == 0) return;
+    if (st->nactive == 0 || threadIdx.x >= 32) return;
     double pq[6];
-    case_pq_all(ad, pq);
+    case_pq_warp(ad, pq);
     // lane k of warp 0 handles load case k (the state loads run in parallel)
     if (threadIdx.x < 32) {
         const int k = threadIdx.x;
@@ -259,9 +249,9 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kerne
         }
     }
     store_block_pair<T>(drz, drr, a.partial);
-    if (!last_block_ticket(&st->ticket_update, gridDim.x)) return;
+    if (!last_block_ticket(&st->ticket_update, gridDim.x) || threadIdx.x >= 32) return;
     double tot[12];
-    sum_case_partials(a.partial, g.bpk, tot);
+    sum_case_partials_warp(a.partial, g.bpk, tot);
     // lane kk of warp 0 handles load case kk (the state loads run in parallel)
     if (threadIdx.x < 32) {
         const int kk = threadIdx.x;
@@ -341,9 +331,9 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_jacobi_rz_ke
         }
     }
     store_block_pair<float>(drz, dnone, a.partial);
-    if (!last_block_ticket(&st->ticket_aux, gridDim.x)) return;
+    if (!last_block_ticket(&st->ticket_aux, gridDim.x) || threadIdx.x >= 32) return;
     double tot[12];
-    sum_case_partials(a.partial, g.bpk, tot);
+    sum_case_partials_warp(a.partial, g.bpk, tot);
     if (threadIdx.x < 32) {
         const int kk = threadIdx.x;
         int act = 0;
