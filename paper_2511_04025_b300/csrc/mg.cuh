@@ -399,6 +399,83 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__r
     }
 }
 
+// The same stencil, one thread per (node, load case).  A block takes 32
+// consecutive nodes and the six load cases (warp w = load case w): it first
+// copies the 32 nodes' stencils (contiguous, 31 KB) into shared memory with
+// 16-byte loads, then each thread accumulates its three output components
+// over the 27 offsets from shared memory (node stride 243 floats: lanes hit
+// distinct banks) and three coalesced loads of x per offset.  No warp
+// reduce-scatter, ~3.5x fewer instructions than one warp per node, and six
+// warps per 32 nodes of parallelism.
+constexpr int kStencilNodes = 32;
+__global__ void __launch_bounds__(6 * kStencilNodes) mg_stencil_nc_kernel(int r, const float *__restrict__ S,
+                                                                        const float *__restrict__ x,
+                                                                        const float *__restrict__ b,
+                                                                        const float *__restrict__ Dinv, float w,
+                                                                        int mode, float *__restrict__ out,
+                                                                        const PcgState *st) {
+    __shared__ __align__(16) float sS[kStencilNodes * 243];
+    pdl_enter();
+    if (mg_done(st)) return;
+    const unsigned N = (unsigned)r * r * r;
+    const unsigned n0 = blockIdx.x * kStencilNodes;
+    const unsigned nn = min((unsigned)kStencilNodes, N - n0);
+    {
+        const unsigned cnt = nn * 243;  // n0 * 243 floats is a multiple of 4 (n0 a multiple of 32)
+        const float4 *src = reinterpret_cast<const float4 *>(S + (size_t)n0 * 243);
+        float4 *dst = reinterpret_cast<float4 *>(sS);
+        for (unsigned i = threadIdx.x; i < cnt / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+        for (unsigned i = (cnt / 4) * 4 + threadIdx.x; i < cnt; i += blockDim.x) sS[i] = __ldg(S + (size_t)n0 * 243 + i);
+    }
+    __syncthreads();
+    const int k = threadIdx.x / kStencilNodes, lane = threadIdx.x % kStencilNodes;
+    if ((unsigned)lane >= nn) return;
+    if (st && !st->active[k]) return;
+    const unsigned n = n0 + lane;
+    const int ix = (int)(n % (unsigned)r), iy = (int)((n / (unsigned)r) % (unsigned)r), iz = (int)(n / ((unsigned)r * r));
+    const float *x0p = x + (size_t)(3 * k) * N, *x1p = x0p + N, *x2p = x1p + N;
+    const float *B = sS + lane * 243;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        const unsigned zz = (unsigned)wrap_l(iz + dz, r);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const unsigned row = (zz * r + (unsigned)wrap_l(iy + dy, r)) * r;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const unsigned j = row + (unsigned)wrap_l(ix + dx, r);
+                const int dl = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                const float v0 = __ldg(x0p + j), v1 = __ldg(x1p + j), v2 = __ldg(x2p + j);
+                const float *Bd = B + dl * 9;
+                a0 += Bd[0] * v0 + Bd[1] * v1 + Bd[2] * v2;
+                a1 += Bd[3] * v0 + Bd[4] * v1 + Bd[5] * v2;
+                a2 += Bd[6] * v0 + Bd[7] * v1 + Bd[8] * v2;
+            }
+        }
+    }
+    const size_t o = (size_t)(3 * k) * N + n;
+    if (mode == 0) {
+        out[o] = a0;
+        out[o + N] = a1;
+        out[o + 2 * (size_t)N] = a2;
+        return;
+    }
+    const float r0 = b[o] - a0, r1 = b[o + N] - a1, r2 = b[o + 2 * (size_t)N] - a2;
+    if (mode == 1) {
+        out[o] = r0;
+        out[o + N] = r1;
+        out[o + 2 * (size_t)N] = r2;
+        return;
+    }
+    float D[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) D[m] = __ldg(Dinv + (size_t)m * N + n);
+    out[o] = x[o] + w * (D[0] * r0 + D[1] * r1 + D[2] * r2);
+    out[o + N] = x[o + N] + w * (D[3] * r0 + D[4] * r1 + D[5] * r2);
+    out[o + 2 * (size_t)N] = x[o + 2 * (size_t)N] + w * (D[6] * r0 + D[7] * r1 + D[8] * r2);
+}
+
 // bc = R (bf - tf): coarse node I gathers w(a) (bf - tf)[2I + a] over its 27
 // fine neighbours; tf may be null (bf is then the residual itself).  Grid:
 // x over coarse nodes (one per thread), y over the 18 planes.  Each of the 9

@@ -604,6 +604,20 @@ inline int mg_child_matrices(shl_ctx *ctx, double nu, cudaStream_t s, float **ou
     return SHL_OK;
 }
 
+// Stencil pass on one coarse level: one thread per (node, load case) with the
+// stencils staged in shared memory from 32^3 nodes up (bandwidth and issue
+// bound), one warp per node below (latency bound: few nodes, and the warp form
+// keeps more loads in flight per node).  The caller counts the launch.
+inline void launch_stencil(const MgLevel &L, const float *x, const float *b, float w, int mode, float *out,
+                           const PcgState *st, cudaStream_t s) {
+    if (L.N >= 32768)
+        pdl_launch(mg_stencil_nc_kernel, (unsigned)((L.N + kStencilNodes - 1) / kStencilNodes), 6 * kStencilNodes, 0, s,
+                   L.r, (const float *)L.S, x, b, (const float *)L.Dinv, w, mode, out, st);
+    else
+        pdl_launch(mg_stencil_kernel, grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s, L.r, (const float *)L.S, x, b,
+                   (const float *)L.Dinv, w, mode, out, st);
+}
+
 inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opts *o, Mg *mg, cudaStream_t s) {
     float *childM = nullptr;
     SHL_TRY(mg_child_matrices(ctx, o->nu, s, &childM));
@@ -675,8 +689,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     a.pin = 1;
                     SHL_TRY(launch_apply<float>(ctx, a, s));
                 } else {
-                    pdl_launch(mg_stencil_kernel, grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s, L.r, L.S, x, nullptr,
-                               nullptr, 1.0f, 0, L.t, nullptr);
+                    launch_stencil(L, x, nullptr, 1.0f, 0, L.t, nullptr, s);
                 }
                 const int g = grid1d(L.N, kBlk, 148 * 8);
                 mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + it);
@@ -819,8 +832,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     };
     auto sweep = [&](MgLevel &L, int mode) {  // coarse level: mode 1 residual into t, mode 2 Jacobi sweep
         float *out = mode == 1 ? L.t : (L.x == L.xa ? L.xb : L.xa);
-        pdl_launch(mg_stencil_kernel, grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s, L.r, L.S, L.x, L.b, L.Dinv,
-                   L.omega, mode, out, st);
+        launch_stencil(L, L.x, L.b, L.omega, mode, out, st, s);
         ++ctx->launches;
         if (mode == 2) L.x = out;
     };
