@@ -54,6 +54,7 @@ struct shl_ctx {
     // and freed stream-ordered there (no device-wide synchronisation, which
     // would disturb other slots' CUDA-graph captures)
     bool stream_ordered_alloc = false;
+    void *pinned = nullptr;  // host staging of the multigrid setup (page-locked, allocated once)
 };
 
 namespace shl {
@@ -140,6 +141,10 @@ inline void ws_free_all(shl_ctx *ctx) {
         }
     if (ctx->stream_ordered_alloc) cudaStreamSynchronize(ctx->stream);
     ctx->ws.slots.clear();
+    if (ctx->pinned) {
+        cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+    }
 }
 
 inline cudaStream_t pick_stream(shl_ctx *ctx, void *s) { return s ? static_cast<cudaStream_t>(s) : ctx->stream; }

@@ -580,11 +580,7 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(int rc, const float *__
 // ---- lambda_max(D^-1 A) by power iteration (sets the damping per level) ----
 // Uses the first three planes (one load case).
 __global__ void mg_power_seed_kernel(size_t N, float *x) {
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < 18 * N; n += (size_t)gridDim.x * blockDim.x) {
-        if (n >= 3 * N) {
-            x[n] = 0.0f;
-            continue;
-        }
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < 3 * N; n += (size_t)gridDim.x * blockDim.x) {
         unsigned h = (unsigned)n * 2654435761u + 0x9e3779b9u;
         h ^= h >> 15;
         h *= 2246822519u;
@@ -617,6 +613,15 @@ __global__ void mg_power_dinv_kernel(size_t N, const float *t, const float *Dinv
 }
 
 // x = y / ||y|| on planes 0..2
+// State of the power iteration: one vector (load case 0), so the coarse
+// stencil passes skip the other five.
+__global__ void mg_power_state_kernel(PcgState *st) {
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) st->active[k] = k == 0;
+        st->nactive = 1;
+    }
+}
+
 __global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nrm2, float *x) {
     const float inv = (float)(1.0 / sqrt(nrm2[0] > 0.0 ? nrm2[0] : 1.0));
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < 3 * N; n += (size_t)gridDim.x * blockDim.x)

@@ -663,23 +663,47 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         ctx->launches += 2;
     }
     SHL_CUDA(ctx, cudaGetLastError());
-    // damping per smoothed level from lambda_max(D^-1 A) (power iteration)
+    // Page-locked host staging (allocated once per context at its largest
+    // size): [coarsest stencil | power-iteration norms | coarse factor upload]
+    constexpr int kPow = 15;
+    const size_t pin_s = (size_t)kMgMaxCoarse * 243 * sizeof(float);
+    const size_t pin_w = (size_t)kMgMaxLevels * kPow * sizeof(double);
+    const size_t pin_y = (size_t)2 * (3 * kMgMaxCoarse) * (3 * kMgMaxCoarse) * sizeof(float);
+    if (!ctx->pinned) SHL_CUDA(ctx, cudaMallocHost(&ctx->pinned, pin_s + pin_w + pin_y));
+    float *hS = static_cast<float *>(ctx->pinned);
+    double *hpw = reinterpret_cast<double *>(static_cast<char *>(ctx->pinned) + pin_s);
+    float *hY = reinterpret_cast<float *>(static_cast<char *>(ctx->pinned) + pin_s + pin_w);
+    // the coarsest stencil goes to the host first; the host assembles and
+    // factors the coarse operator while the GPU runs the power iterations
+    const MgLevel &C = mg->lv[mg->L];
+    const int n3 = (int)(3 * C.N);
+    mg->n3 = n3;
+    SHL_CUDA(ctx, cudaMemcpyAsync(hS, C.S, C.N * 243 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    cudaEvent_t s_ready = nullptr;
+    SHL_CUDA(ctx, cudaEventCreateWithFlags(&s_ready, cudaEventDisableTiming));
+    SHL_CUDA(ctx, cudaEventRecord(s_ready, s));
+    // damping per smoothed level from lambda_max(D^-1 A) (power iteration on
+    // one vector, every level enqueued before a single read of the norms)
     {
         ElemOp<float> op32;
         SHL_TRY(get_op(ctx, o->nu, r, &op32));
         double *pw = nullptr, *ppart = nullptr;
         unsigned *ptick = nullptr;
         float *py = nullptr;
-        SHL_TRY(ws_get_t(ctx, "mg_pow", 64, &pw));
+        PcgState *pst = nullptr;
+        SHL_TRY(ws_get_t(ctx, "mg_pow", (size_t)kMgMaxLevels * kPow, &pw));
         SHL_TRY(ws_get_t(ctx, "mg_pow_partial", (size_t)148 * 8, &ppart));
         SHL_TRY(ws_get_t(ctx, "mg_pow_ticket", 1, &ptick));
         SHL_TRY(ws_get_t(ctx, "mg_pow_y", 3 * mg->lv[0].N, &py));
-        const int kPow = 15;
+        SHL_TRY(ws_get_t(ctx, "mg_pow_state", 1, &pst));
+        mg_power_state_kernel<<<1, 32, 0, s>>>(pst);
+        ++ctx->launches;
         for (int l = 0; l < mg->L; ++l) {
             MgLevel &L = mg->lv[l];
             float *x = l == 0 ? nullptr : L.x;
             if (l == 0) SHL_TRY(ws_get_t(ctx, "z32", 18 * L.N, &x));
-            mg_power_seed_kernel<<<grid1d(18 * L.N), kBlk, 0, s>>>(L.N, x);
+            mg_power_seed_kernel<<<grid1d(3 * L.N), kBlk, 0, s>>>(L.N, x);
+            ++ctx->launches;
             for (int it = 0; it < kPow; ++it) {
                 if (l == 0) {
                     ApplyArgs<float> a = make_apply<float>(r, den, op32);
@@ -689,28 +713,22 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     a.pin = 1;
                     SHL_TRY(launch_apply<float>(ctx, a, s));
                 } else {
-                    launch_stencil(L, x, nullptr, 1.0f, 0, L.t, nullptr, s);
+                    launch_stencil(L, x, nullptr, 1.0f, 0, L.t, pst, s);
+                    ++ctx->launches;
                 }
                 const int g = grid1d(L.N, kBlk, 148 * 8);
-                mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + it);
-                mg_power_scale_kernel<<<grid1d(3 * L.N), kBlk, 0, s>>>(L.N, py, pw + it, x);
-                ctx->launches += 3;
+                mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + l * kPow + it);
+                mg_power_scale_kernel<<<grid1d(3 * L.N), kBlk, 0, s>>>(L.N, py, pw + l * kPow + it, x);
+                ctx->launches += 2;
             }
-            double hpw[kPow];
-            SHL_CUDA(ctx, cudaMemcpyAsync(hpw, pw, sizeof(hpw), cudaMemcpyDeviceToHost, s));
-            SHL_CUDA(ctx, cudaStreamSynchronize(s));
-            const double lam = std::sqrt(hpw[kPow - 1]);
-            const double base = o->mg_omega > 0.0 ? o->mg_omega : 1.4;  // omega * lambda_max
-            L.omega = (float)(lam > 0.0 && std::isfinite(lam) ? base / lam : 0.3);
         }
+        SHL_CUDA(ctx, cudaMemcpyAsync(hpw, pw, (size_t)mg->L * kPow * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
-    // coarsest: dense, coarse node 0 pinned, inverted in FP64 on the host
-    const MgLevel &C = mg->lv[mg->L];
-    const int n3 = (int)(3 * C.N);
-    mg->n3 = n3;
-    std::vector<float> Sh(C.N * 243);
-    SHL_CUDA(ctx, cudaMemcpyAsync(Sh.data(), C.S, Sh.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
-    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    // coarsest: dense, coarse node 0 pinned, factored in FP64 on the host
+    const cudaError_t se = cudaEventSynchronize(s_ready);
+    cudaEventDestroy(s_ready);
+    if (se != cudaSuccess) return set_err(ctx, SHL_ECUDA, "coarse stencil copy: %s", cudaGetErrorString(se));
+    const float *Sh = hS;
     const int m = n3 - 3;  // pinned: DOFs of node 0 removed
     std::vector<double> A((size_t)m * m, 0.0);
     const int rc = C.r;
@@ -794,8 +812,8 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         const double inv = 1.0 / Lc[(size_t)i * m + i];
         for (int c = 0; c <= i; ++c) yi[c] *= inv;
     }
-    std::vector<float> Yf((size_t)2 * n3 * n3, 0.0f);
-    float *YTf = Yf.data() + (size_t)n3 * n3;
+    float *Yf = hY, *YTf = hY + (size_t)n3 * n3;
+    std::memset(hY, 0, sizeof(float) * 2 * (size_t)n3 * n3);
     for (int a = 0; a < m; ++a)
         for (int c = 0; c <= a; ++c) {
             const float v = (float)Y[(size_t)a * m + c];
@@ -805,8 +823,14 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     SHL_TRY(ws_get_t(ctx, "mg_Y", (size_t)2 * n3 * n3 + (size_t)6 * n3, &mg->Y));
     mg->YT = mg->Y + (size_t)n3 * n3;
     mg->w = mg->YT + (size_t)n3 * n3;
-    SHL_CUDA(ctx, cudaMemcpyAsync(mg->Y, Yf.data(), Yf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    SHL_CUDA(ctx, cudaMemcpyAsync(mg->Y, hY, sizeof(float) * 2 * (size_t)n3 * n3, cudaMemcpyHostToDevice, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    // smoother damping from the power iterations' last Rayleigh estimate
+    for (int l = 0; l < mg->L; ++l) {
+        const double lam = std::sqrt(hpw[l * kPow + kPow - 1]);
+        const double base = o->mg_omega > 0.0 ? o->mg_omega : 1.4;  // omega * lambda_max
+        mg->lv[l].omega = (float)(lam > 0.0 && std::isfinite(lam) ? base / lam : 0.3);
+    }
     return SHL_OK;
 }
 
