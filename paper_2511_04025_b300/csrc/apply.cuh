@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
         // (-4 h eps_id) are non-zero.
         T ch0[3], chd[3][3];
         if (RESID) {
-            const T h4 = T(4) / T(r);
+            const T h4 = T(4.0 / (double)r);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 T sum = T(0);
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
             const size_t e = (size_t)(ez < 0 ? ez + r : (ez >= r ? ez - r : ez)) * rr + exy;
             T Ee;
             if constexpr (SMOOTH)
-                Ee = (T)(a.Evoid + a.rho[e] * (a.E - a.Evoid));
+                Ee = T((double)a.Evoid + a.rho[e] * ((double)a.E - (double)a.Evoid));
             else
                 Ee = a.mask[e] ? a.E : a.Evoid;
             return RESID ? -Ee : Ee;

@@ -239,6 +239,51 @@ __device__ inline void block_sum_df(const float2 (&v)[NV], double (&out)[NV]) {
     for (int k = 0; k < NV; ++k) out[k] = res[k];
 }
 
+// Double-float number (hi + lo, |lo| <= ulp(hi) / 2; about 48 significant
+// bits) with FP32 arithmetic only: sums by TwoSum, products by the FMA-exact
+// product error (Dekker, Knuth; the sloppy double-float addition, whose error
+// is bounded relative to the operands, which a residual f - K x needs).  The
+// FP32-with-refinement solver forms its true residuals in this type: on B300
+// that is ~3x faster than FP64, whose pipe is narrow.
+struct __align__(8) dfloat {
+    float hi, lo;
+    dfloat() = default;
+    __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dfloat(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+    const float hi = s + e;
+    return dfloat(hi, e - (hi - s));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const float hi = p + e;
+    return dfloat(hi, e - (hi - p));
+}
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
+
+// Conversions of the 18 planes (N values each) of the load cases in `mask`.
+__global__ void to_dfloat_kernel(size_t N, int mask, const double *__restrict__ x, dfloat *__restrict__ y) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 18 * N; i += (size_t)gridDim.x * blockDim.x)
+        if ((mask >> (i / N / 3)) & 1) y[i] = dfloat(x[i]);
+}
+// in place: element i is read as a dfloat and written back as a double
+__global__ void dfloat_to_double_kernel(size_t N, int mask, double *xy) {
+    const dfloat *y = reinterpret_cast<const dfloat *>(xy);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 18 * N; i += (size_t)gridDim.x * blockDim.x)
+        if ((mask >> (i / N / 3)) & 1) {
+            const dfloat v = y[i];
+            xy[i] = (double)v;
+        }
+}
+
 // Per-thread dot-product accumulator.  FP64 vectors accumulate in FP64.  FP32
 // vectors accumulate each thread's few products with compensated (Kahan)
 // FP32 summation and hand the result to the FP64 block/grid reduction: the
@@ -251,6 +296,12 @@ struct DotAcc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double x) { s += x; }
     __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct DotAcc<dfloat> {
+    dfloat s = dfloat(0.0f, 0.0f);
+    __device__ __forceinline__ void add(dfloat x) { s += x; }
+    __device__ __forceinline__ double get() const { return (double)s; }
 };
 template <>
 struct DotAcc<float> {

@@ -526,8 +526,37 @@ struct SolveOut {
 // the pinned system; x == nullptr means x = 0 (the loads f themselves).
 // out = f - K x (pinned), FP64, for the load cases in mask (others untouched),
 // and |out|^2 per computed case into dot_out.
+// With opdf the residual is formed in double-float arithmetic (x converted on
+// the way in, the result converted back in place): ~3x faster than FP64 on
+// B300 and far more accurate than the refinement needs.  The FP64 solver
+// keeps FP64.
 inline int resid64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double> &op, const double *x, double *out,
-                   int pin, double *dot_out, cudaStream_t s, int mask = 0x3f) {
+                   int pin, double *dot_out, cudaStream_t s, int mask = 0x3f, const ElemOp<dfloat> *opdf = nullptr) {
+    if (opdf) {
+        const size_t N = (size_t)r * r * r;
+        dfloat *xdf = nullptr;
+        double *partial = nullptr;
+        if (x) SHL_TRY(ws_get_t(ctx, "resid_xdf", 18 * N, &xdf));
+        const size_t rows = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<dfloat>(r, 6) * 6;
+        SHL_TRY(ws_get_t(ctx, "resid_partial", rows * 6, &partial));
+        if (x) {  // x == null: the residual of the zero iterate (the loads)
+            to_dfloat_kernel<<<grid1d(18 * N, kBlk, 148 * 8), kBlk, 0, s>>>(N, mask, x, xdf);
+            ++ctx->launches;
+        }
+        ApplyArgs<dfloat> a = make_apply<dfloat>(r, den, *opdf);
+        a.case_mask = mask;
+        a.p = xdf;
+        a.q = reinterpret_cast<dfloat *>(out);
+        a.pin = pin;
+        a.resid = 1;
+        a.dot = 2;
+        a.dot_out = dot_out;
+        a.partial = partial;
+        SHL_TRY(launch_apply<dfloat>(ctx, a, s));
+        dfloat_to_double_kernel<<<grid1d(18 * N, kBlk, 148 * 8), kBlk, 0, s>>>(N, mask, out);
+        ++ctx->launches;
+        return SHL_OK;
+    }
     ApplyArgs<double> a = make_apply<double>(r, den, op);
     a.case_mask = mask;
     a.p = x;
@@ -924,12 +953,19 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
     SHL_TRY(host_pinned(ctx, &hp));
     ElemOp<double> op64;
     SHL_TRY(get_op(ctx, o->nu, r, &op64));
+    // the FP32 + refinement mode forms its true residuals in double-float
+    ElemOp<dfloat> opdf_v;
+    const ElemOp<dfloat> *opdf = nullptr;
+    if (o->precision == SHL_FP32_REFINE) {
+        SHL_TRY(get_op(ctx, o->nu, r, &opdf_v));
+        opdf = &opdf_v;
+    }
     double *r64 = nullptr, *norms = nullptr;
     SHL_TRY(ws_get_t(ctx, "r64", NV, &r64));
     SHL_TRY(ws_get_t(ctx, "norms", 32, &norms));  // [0:6] |f|^2, [12:18] |f - K x|^2 (pinned system)
     if (!warm) SHL_CUDA(ctx, cudaMemsetAsync(x64, 0, NV * sizeof(double), s));
     // ||f||^2 of the pinned system (r64 = f afterwards)
-    SHL_TRY(resid64(ctx, r, den, op64, nullptr, r64, 1, norms + 0, s));
+    SHL_TRY(resid64(ctx, r, den, op64, nullptr, r64, 1, norms + 0, s, 0x3f, opdf));
     double fpin[6];
     SHL_CUDA(ctx, cudaMemcpyAsync(fpin, norms, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
@@ -991,8 +1027,12 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         const double h_one[8] = {1, 1, 1, 1, 1, 1, 1, 1};
         SHL_CUDA(ctx, cudaMemcpyAsync(one, h_one, sizeof(h_one), cudaMemcpyHostToDevice, s));
         const double delta = o->inner_tol > 0.0 ? o->inner_tol : 1e-4;
-        // r64 = f - K x64 (pinned); r32 = float(r64); x32 = 0
-        SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+        // r64 = f - K x64 (pinned; already f, with |f|^2, for a cold start);
+        // r32 = float(r64); x32 = 0
+        if (warm)
+            SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, 0x3f, opdf));
+        else
+            SHL_CUDA(ctx, cudaMemcpyAsync(norms + 12, norms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s));
         refine_scatter_kernel<<<grid1d(N), kBlk, 0, s>>>(N, r64, one, 0x3f, b.r, b.x);
         ++ctx->launches;
         pcg_config_kernel<<<1, 32, 0, s>>>(st, tol * tol, maxit, 1);
@@ -1089,7 +1129,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                     ++updates;
                     reliable_fold_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, x64, mask);
                     ++ctx->launches;
-                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, mask));
+                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, mask, opdf));
                     reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, r64, mask, restart, rr_true);
                     ++ctx->launches;
                     if (use_mg) {  // direction restarts from the preconditioned true residual
@@ -1120,7 +1160,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
     // computes it every pass; in FP32 + refinement each load case stops at a
     // reliable update, after which its FP64 iterate no longer changes), so an
     // FP64 apply is spent here only after a numeric breakdown.
-    if (out->status == SHL_ENUMERIC) SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s));
+    if (out->status == SHL_ENUMERIC) SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, 0x3f, opdf));
     double hn[24];
     SHL_CUDA(ctx, cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
