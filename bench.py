@@ -47,7 +47,7 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per launch of the FP32 stiffness apply at 64^3,
 # from one `ncu --set full` capture of `bench.py --kernel apply --r 64`; reset
 # to None whenever the kernel changes.
-APPLY_TRAFFIC_64 = None
+APPLY_TRAFFIC_64 = 19_192_576
 
 
 def peaks():
