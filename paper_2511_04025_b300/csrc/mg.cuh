@@ -476,12 +476,41 @@ __global__ void __launch_bounds__(6 * kStencilNodes) mg_stencil_nc_kernel(int r,
     out[o + 2 * (size_t)N] = x[o + 2 * (size_t)N] + w * (D[6] * r0 + D[7] * r1 + D[8] * r2);
 }
 
+// One fine plane restricted to coarse node (ix, iy, iz): the weights w(a) of
+// the 27 fine neighbours 2I + a (1 on the node, 1/2 per odd offset).  Each of
+// the 9 fine rows is read as one 8-byte pair (2ix, 2ix + 1); the left
+// neighbour 2ix - 1 is the previous lane's right value when that lane holds
+// ix - 1 of the same row.  Every lane of the warp must call it (shuffles).
+__device__ __forceinline__ float restrict_plane(const float *__restrict__ bm, const float *__restrict__ tm, int ix,
+                                                const unsigned (&zo)[3], const unsigned (&yo)[3], int rf,
+                                                bool left_in_warp) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int az = 0; az < 3; ++az)
+#pragma unroll
+        for (int ay = 0; ay < 3; ++ay) {
+            const unsigned row = zo[az] + yo[ay];
+            float2 c = *reinterpret_cast<const float2 *>(bm + row + 2 * ix);
+            if (tm) {
+                const float2 t = *reinterpret_cast<const float2 *>(tm + row + 2 * ix);
+                c.x -= t.x;
+                c.y -= t.y;
+            }
+            float left = __shfl_up_sync(0xffffffffu, c.y, 1);
+            if (!left_in_warp) {
+                const unsigned xl = (unsigned)wrap_l(2 * ix - 1, rf);
+                left = tm ? bm[row + xl] - tm[row + xl] : bm[row + xl];
+            }
+            const float rowsum = c.x + 0.5f * (left + c.y);
+            acc += (az == 1 ? 1.0f : 0.5f) * (ay == 1 ? 1.0f : 0.5f) * rowsum;
+        }
+    return acc;
+}
+
 // bc = R (bf - tf): coarse node I gathers w(a) (bf - tf)[2I + a] over its 27
 // fine neighbours; tf may be null (bf is then the residual itself).  Grid:
-// x over coarse nodes (one per thread), y over the 18 planes.  Each of the 9
-// fine rows is read as one 8-byte pair (2ix, 2ix + 1); the left neighbour
-// 2ix - 1 is the previous lane's right value when that lane holds ix - 1 of
-// the same row.  Converged load cases are skipped.
+// x over coarse nodes (one per thread), y over the 18 planes.  Converged load
+// cases are skipped.
 __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *__restrict__ bf,
                                                           const float *__restrict__ tf, float *__restrict__ bc,
                                                           const PcgState *st) {
@@ -509,28 +538,55 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *_
                                 (unsigned)wrap_l(2 * iz + 1, rf) * rrf};
         const unsigned yo[3] = {(unsigned)wrap_l(2 * iy - 1, rf) * rf, (unsigned)(2 * iy) * rf,
                                 (unsigned)wrap_l(2 * iy + 1, rf) * rf};
-        const bool left_in_warp = lane > 0 && ix > 0;
-        float acc = 0.0f;
-#pragma unroll
-        for (int az = 0; az < 3; ++az)
-#pragma unroll
-            for (int ay = 0; ay < 3; ++ay) {
-                const unsigned row = zo[az] + yo[ay];
-                float2 c = *reinterpret_cast<const float2 *>(bm + row + 2 * ix);
-                if (tm) {
-                    const float2 t = *reinterpret_cast<const float2 *>(tm + row + 2 * ix);
-                    c.x -= t.x;
-                    c.y -= t.y;
-                }
-                float left = __shfl_up_sync(0xffffffffu, c.y, 1);
-                if (!left_in_warp) {
-                    const unsigned xl = (unsigned)wrap_l(2 * ix - 1, rf);
-                    left = tm ? bm[row + xl] - tm[row + xl] : bm[row + xl];
-                }
-                const float rowsum = c.x + 0.5f * (left + c.y);
-                acc += (az == 1 ? 1.0f : 0.5f) * (ay == 1 ? 1.0f : 0.5f) * rowsum;
-            }
+        const float acc = restrict_plane(bm, tm, ix, zo, yo, rf, lane > 0 && ix > 0);
         if (valid) bc[(size_t)m * Nc + I] = acc;
+    }
+}
+
+// The same restriction for the three planes of load case k = grid y, followed
+// by the coarse level's first damped block-Jacobi step from a zero iterate,
+// xc = w Dc^-1 bc: the down-leg of the V-cycle needs no separate Jacobi launch
+// on a coarse level that is smoothed.
+__global__ void __launch_bounds__(256) mg_restrict_jacobi_kernel(int rc, const float *__restrict__ bf,
+                                                                 const float *__restrict__ tf, float *__restrict__ bc,
+                                                                 const float *__restrict__ Dc, float w,
+                                                                 float *__restrict__ xc, const PcgState *st) {
+    pdl_enter();
+    if (mg_done(st)) return;
+    const int k = blockIdx.y;
+    if (st && !st->active[k]) return;
+    const unsigned Nc = (unsigned)rc * rc * rc;
+    const int rf = 2 * rc;
+    const unsigned rrf = (unsigned)rf * rf;
+    const size_t Nf = (size_t)rrf * rf;
+    const int lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    const unsigned iters = (Nc + stride - 1) / stride;
+    for (unsigned it = 0; it < iters; ++it) {
+        const unsigned I = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool valid = I < Nc;
+        const unsigned Iv = valid ? I : 0;
+        const int ix = (int)(Iv % (unsigned)rc), iy = (int)((Iv / (unsigned)rc) % (unsigned)rc),
+                  iz = (int)(Iv / ((unsigned)rc * rc));
+        const unsigned zo[3] = {(unsigned)wrap_l(2 * iz - 1, rf) * rrf, (unsigned)(2 * iz) * rrf,
+                                (unsigned)wrap_l(2 * iz + 1, rf) * rrf};
+        const unsigned yo[3] = {(unsigned)wrap_l(2 * iy - 1, rf) * rf, (unsigned)(2 * iy) * rf,
+                                (unsigned)wrap_l(2 * iy + 1, rf) * rf};
+        float b3[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t m = (size_t)(3 * k + i);
+            b3[i] = restrict_plane(bf + m * Nf, tf ? tf + m * Nf : nullptr, ix, zo, yo, rf, lane > 0 && ix > 0);
+        }
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (size_t)(3 * k + i) * Nc + I;
+                bc[o] = b3[i];
+                xc[o] = w * (Dc[(size_t)(3 * i) * Nc + I] * b3[0] + Dc[(size_t)(3 * i + 1) * Nc + I] * b3[1] +
+                             Dc[(size_t)(3 * i + 2) * Nc + I] * b3[2]);
+            }
+        }
     }
 }
 

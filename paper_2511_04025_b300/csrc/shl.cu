@@ -892,10 +892,21 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     mg->lv[0].b = const_cast<float *>(b0);
     mg->lv[0].x = x0;
     for (int l = 1; l <= mg->L; ++l) mg->lv[l].x = mg->lv[l].xa;
+    // restriction into level l + 1; a level that is smoothed (l + 1 < L) also
+    // gets its first Jacobi step x = w D^-1 b there
+    auto restrict_to = [&](int l, const float *bf, const float *tf) {
+        MgLevel &Cl = mg->lv[l + 1];
+        if (l + 1 < mg->L)
+            pdl_launch(mg_restrict_jacobi_kernel, dim3(grid1d(Cl.N, kBlk, 148), 6), kBlk, 0, s, Cl.r, bf, tf, Cl.b,
+                       (const float *)Cl.Dinv, Cl.omega, Cl.x, st);
+        else
+            pdl_launch(mg_restrict_kernel, dim3(grid1d(Cl.N, kBlk, 148), 18), kBlk, 0, s, Cl.r, bf, tf, Cl.b, st);
+        ++ctx->launches;
+    };
     for (int l = 0; l < mg->L; ++l) {  // down: pre-smooth, restrict the residual
         MgLevel &L = mg->lv[l];
         const int g = grid1d(L.N);
-        if (!(l == 0 && (fuse & kVcFirstFused))) {
+        if (l == 0 && !(fuse & kVcFirstFused)) {
             pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
             ++ctx->launches;
         }
@@ -906,15 +917,12 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
                 ++ctx->launches;
             }
             SHL_TRY(fine_apply(L.x, L.t));
-            pdl_launch(mg_restrict_kernel, dim3(grid1d(mg->lv[1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[1].r, L.b,
-                       L.t, mg->lv[1].b, st);
+            restrict_to(0, L.b, L.t);
         } else {
             for (int it = 1; it < mg->nu; ++it) sweep(L, 2);
             sweep(L, 1);
-            pdl_launch(mg_restrict_kernel, dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[l + 1].r,
-                       L.t, nullptr, mg->lv[l + 1].b, st);
+            restrict_to(l, L.t, nullptr);
         }
-        ++ctx->launches;
     }
     {
         MgLevel &C = mg->lv[mg->L];
