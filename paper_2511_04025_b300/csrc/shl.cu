@@ -1182,16 +1182,43 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
     return SHL_OK;
 }
 
+// C^H from the displacements u (FP64).  With df the element energies are
+// summed in double-float arithmetic (the FP32 + refinement mode), else in FP64.
 inline int run_chom(shl_ctx *ctx, int r, const Density &den, double nu, const double *u, double *C_dev,
-                    cudaStream_t s) {
-    ElemOp<double> op;
-    SHL_TRY(get_op(ctx, nu, r, &op));
+                    cudaStream_t s, bool df = false) {
     const size_t N = (size_t)r * r * r;
     const int g = grid1d(N, kChomThreads, 148 * 8);
     double *partial = nullptr;
     unsigned *ticket = nullptr;
     SHL_TRY(ws_get_t(ctx, "chom_partial", (size_t)g * 21, &partial));
     SHL_TRY(ws_get_t(ctx, "chom_ticket", 1, &ticket));
+    if (df) {
+        ElemOp<dfloat> opd;
+        SHL_TRY(get_op(ctx, nu, r, &opd));
+        dfloat *udf = nullptr;
+        SHL_TRY(ws_get_t(ctx, "resid_xdf", 18 * N, &udf));
+        to_dfloat_kernel<<<grid1d(18 * N, kBlk, 148 * 8), kBlk, 0, s>>>(N, 0x3f, u, udf);
+        ChomDfArgs a{};
+        a.r = r;
+        a.N = N;
+        a.u = udf;
+        a.mask = den.mask;
+        a.rho = den.rho;
+        a.E = den.E;
+        a.Evoid = den.Ev;
+        a.partial = partial;
+        a.ticket = ticket;
+        a.C = C_dev;
+        a.op = opd;
+        const size_t smem = sizeof(dfloat) * 6 * 24 * kChomThreads;
+        raise_smem_limit((const void *)chom_df_kernel, smem);
+        chom_df_kernel<<<g, kChomThreads, smem, s>>>(a);
+        ctx->launches += 2;
+        SHL_CUDA(ctx, cudaGetLastError());
+        return SHL_OK;
+    }
+    ElemOp<double> op;
+    SHL_TRY(get_op(ctx, nu, r, &op));
     ChomArgs a{};
     a.r = r;
     a.N = N;
@@ -1257,7 +1284,7 @@ inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double
     cudaEventRecord(e1, s);
     double *Cd = nullptr;
     if (rc == SHL_OK) rc = ws_get_t(ctx, "chom_out", 36, &Cd);
-    if (rc == SHL_OK) rc = run_chom(ctx, r, den, o->nu, x64, Cd, s);
+    if (rc == SHL_OK) rc = run_chom(ctx, r, den, o->nu, x64, Cd, s, o->precision == SHL_FP32_REFINE);
     cudaEventRecord(e2, s);
     if (rc == SHL_OK && C_out) cudaMemcpyAsync(C_out, Cd, 36 * sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
