@@ -126,7 +126,7 @@ typedef struct {
  *                  otherwise, and in SHL_FP64 mode, point Jacobi.
  *   mg_nu          smoothing sweeps before and after the coarse correction (<= 0: 1)
  *   mg_omega       block-Jacobi damping as omega * lambda_max(D^-1 A) per level,
- *                  lambda_max estimated by power iteration at setup (<= 0: 1.4);
+ *                  lambda_max estimated by power iteration at setup (<= 0: 1.6);
  *                  if the preconditioned CG still breaks down, the solve is
  *                  repeated with point Jacobi
  */

@@ -857,7 +857,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     // smoother damping from the power iterations' last Rayleigh estimate
     for (int l = 0; l < mg->L; ++l) {
         const double lam = std::sqrt(hpw[l * kPow + kPow - 1]);
-        const double base = o->mg_omega > 0.0 ? o->mg_omega : 1.4;  // omega * lambda_max
+        const double base = o->mg_omega > 0.0 ? o->mg_omega : 1.6;  // omega * lambda_max
         mg->lv[l].omega = (float)(lam > 0.0 && std::isfinite(lam) ? base / lam : 0.3);
     }
     return SHL_OK;
@@ -1484,7 +1484,7 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->inner_tol = 1e-4;
     o->precond = SHL_PRECOND_MG;
     o->mg_nu = 1;
-    o->mg_omega = 1.4;
+    o->mg_omega = 1.6;
 }
 
 int shl_create(const shl_opts *opts, shl_ctx **out) {
