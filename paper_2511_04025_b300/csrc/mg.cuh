@@ -18,7 +18,9 @@
 // so the V-cycle is a symmetric preconditioner).  Fine level: the matrix-free
 // apply with node 0 pinned (its block-Jacobi inverse is zero, so the pinned
 // DOFs never move).  Coarsest level: the stencil assembled densely on the
-// host, coarse node 0 pinned, inverted in FP64, applied as a dense matvec.
+// host, coarse node 0 pinned, regularised by a small multiple of the
+// all-solid stiffness, factored by Cholesky in FP64 and applied as
+// Y^T (Y b) with the FP32 inverse factor Y = L^-1.
 #pragma once
 
 #include "apply.cuh"
