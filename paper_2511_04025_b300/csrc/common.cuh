@@ -201,11 +201,11 @@ __device__ inline void block_reduce_store(double (&v)[NV], double *partial, int 
 // B300's FP64 pipe is very narrow (one FP64 warp instruction occupies it for
 // ~16 cycles), so an FP64 shuffle tree in every block, or every thread
 // recomputing the same FP64 totals, costs microseconds at a kernel's tail.
-__device__ __forceinline__ float2 two_sum(float a, float b) {
+__host__ __device__ __forceinline__ float2 two_sum(float a, float b) {
     const float s = a + b, bb = s - a;
     return make_float2(s, (a - (s - bb)) + (b - bb));
 }
-__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+__host__ __device__ __forceinline__ float2 df_add(float2 x, float2 y) {
     const float2 t = two_sum(x.x, y.x);
     const float lo = t.y + (x.y + y.y);
     const float hi = t.x + lo;
@@ -252,22 +252,22 @@ struct __align__(8) dfloat {
     __host__ __device__ constexpr dfloat(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
-__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+__host__ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
     const float s = a.hi + b.hi, bb = s - a.hi;
     const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
     const float hi = s + e;
     return dfloat(hi, e - (hi - s));
 }
-__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
-__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
-__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+__host__ __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__host__ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
     const float hi = p + e;
     return dfloat(hi, e - (hi - p));
 }
-__device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
+__host__ __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
 
 // Conversions of the 18 planes (N values each) of the load cases in `mask`.
 __global__ void to_dfloat_kernel(size_t N, int mask, const double *__restrict__ x, dfloat *__restrict__ y) {
