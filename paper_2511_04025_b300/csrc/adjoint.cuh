@@ -119,7 +119,8 @@ __global__ void adj_coef_kernel(int r, int K, const double *__restrict__ QR, dou
         double s = 0.0;
         for (int iz = 0; iz < r; ++iz) {
             const double *pz = phi + (size_t)iz * nb;
-            s += QR[((size_t)iz * 2 + 0) * nb * nb + ab] * pz[cc] + QR[((size_t)iz * 2 + 1) * nb * nb + ab] * basis_deriv(pz, cc, K);
+            s += QR[((size_t)iz * 2 + 0) * nb * nb + ab] * pz[cc] +
+                 QR[((size_t)iz * 2 + 1) * nb * nb + ab] * basis_deriv(pz, cc, K);
         }
         Abar[t] = s;
     }

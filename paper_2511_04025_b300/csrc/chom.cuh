@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(kChomThreads) chom_df_kernel(const ChomDfArgs 
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int m = 0; m < 8; ++m) wdf[((k * 3 + i) * 8 + m) * blockDim.x + threadIdx.x] = w[i][m] + a.op.chihat[k][i][m];
+                for (int m = 0; m < 8; ++m)
+                    wdf[((k * 3 + i) * 8 + m) * blockDim.x + threadIdx.x] = w[i][m] + a.op.chihat[k][i][m];
         }
         int t = 0;
         for (int j = 0; j < 6; ++j) {

@@ -803,7 +803,8 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     }
     // symmetrise (FP32 stencil rounding), Cholesky, inverse factor Y = L^-1
     for (int i = 0; i < m; ++i)
-        for (int j = 0; j < i; ++j) A[(size_t)i * m + j] = A[(size_t)j * m + i] = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
+        for (int j = 0; j < i; ++j)
+            A[(size_t)i * m + j] = A[(size_t)j * m + i] = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
     // A pivot at or below the FP32 rounding level of the stencil sums (a
     // near-rigid mode of a nearly void coarse cell) is raised to that level:
     // L L^T stays SPD whenever L has a positive diagonal, which is all the

@@ -190,7 +190,8 @@ struct FineJacobi {
 //   from vec_jacobi_rz.
 // Last block: iteration count, convergence and budget tests, nactive.
 template <typename T, int V, bool MG>
-__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kernel(VecArgs<T> a, VecGeom g, FineJacobi fj) {
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM)
+    vec_update_kernel(VecArgs<T> a, VecGeom g, FineJacobi fj) {
     pdl_enter();
     PcgState *st = a.st;
     if (st->nactive == 0) return;  // uniform: the solve has finished
@@ -286,8 +287,8 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_update_kerne
 // z += w D^-1 (r - t) (active cases; t = K z from the preceding apply), then
 // rz = r . z; last block: beta = rz / rz_prev, rz_prev = rz.
 template <int V>
-__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_jacobi_rz_kernel(VecArgs<float> a, VecGeom g, FineJacobi fj,
-                                                                    const float *__restrict__ t) {
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM)
+    vec_jacobi_rz_kernel(VecArgs<float> a, VecGeom g, FineJacobi fj, const float *__restrict__ t) {
     pdl_enter();
     PcgState *st = a.st;
     if (st->nactive == 0) return;
