@@ -59,7 +59,7 @@ class InverseDesign:
         self.seed = seed
         self.hist = History()
         self.popsize_used = popsize or 4 + int(3 * math.log(design.pos.size))
-        self._u = torch.empty(18 * r ** 3, dtype=torch.float64, device="cuda")
+        self._u = None  # forward displacements on the device (allocated by the first alpha step)
         self._adam_m = np.zeros(na)
         self._adam_v = np.zeros(na)
         self._adam_t = 0
@@ -92,6 +92,8 @@ class InverseDesign:
         With t fixed the volume moves with alpha, so each step differentiates
         E(C^H, V) with V the smoothed volume fraction of the current design."""
         t = self.thickness()
+        if self._u is None:
+            self._u = torch.empty(18 * self.r ** 3, dtype=torch.float64, device="cuda")
         for _ in range(n):
             fwd = shl.shl_grad(self.h, self.design, self.r, self.opts, np.zeros((6, 6)), u=self._u, t=t)
             _, G, gV = objectives.value_and_grad(self.fn, fwd["C"], fwd["V"])
