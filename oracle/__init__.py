@@ -47,8 +47,12 @@ _ip = ctypes.POINTER(ctypes.c_int)
 def build(force: bool = False) -> str:
     """Compile the C oracle (plain -O2, no fast-math, no FMA contraction)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        # built beside the target and renamed into place: a process that has the
+        # old library loaded keeps its (unlinked) copy
+        tmp = f"{_SO}.{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-                               "-shared", "-Wall", "-o", _SO, _SRC])
+                               "-shared", "-Wall", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
     return _SO
 
 
@@ -71,7 +75,7 @@ def lib():
         L.shlo_element_sensitivity.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                _dp, _dp, _dp]
         L.shlo_field_vjp.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_long, _dp, _dp, _dp, _dp,
-                                     _dp]
+                                     _dp, _dp]
         _lib = L
     return _lib
 
@@ -254,25 +258,30 @@ def element_sensitivity(r: int, u: np.ndarray, G: np.ndarray, E=1.0, nu=0.3, Evo
     return g
 
 
-def field_vjp(design, pts: np.ndarray, Fbar: np.ndarray, gFbar: np.ndarray):
+def field_vjp(design, pts: np.ndarray, Fbar: np.ndarray, gFbar: np.ndarray, want_alpha: bool = False):
     """sum_p Fbar dF/dtheta + gFbar . d(grad F)/dtheta for theta = charge positions
-    (n x 3) and magnitudes (n) (chain rule through Eq. charge-field)."""
+    (n x 3), magnitudes (n) and, with want_alpha, the mode weights alpha_hkl
+    ((K+1)^3, indexed [h][k][l]; Sec. 4.3) (chain rule through Eq. charge-field)."""
     pts = np.ascontiguousarray(pts, dtype=np.float64)
     g_pos = np.zeros((design.n, 3))
     g_q = np.zeros(design.n)
+    g_alpha = np.zeros((design.K + 1) ** 3) if want_alpha else None
     alpha = None if design.alpha is None else np.ascontiguousarray(design.alpha, dtype=np.float64)
     st = lib().shlo_field_vjp(design.n, _p(np.ascontiguousarray(design.pos, dtype=np.float64)),
                               _p(np.ascontiguousarray(design.q, dtype=np.float64)), _p(alpha), design.K,
                               pts.shape[0], _p(pts), _p(np.ascontiguousarray(Fbar, dtype=np.float64)),
-                              _p(np.ascontiguousarray(gFbar, dtype=np.float64)), _p(g_pos), _p(g_q))
+                              _p(np.ascontiguousarray(gFbar, dtype=np.float64)), _p(g_pos), _p(g_q), _p(g_alpha))
     assert st == 0
+    if want_alpha:
+        return g_pos, g_q, g_alpha
     return g_pos, g_q
 
 
 def gradient(design, r: int, dEdC: np.ndarray, t: float, kappa: Optional[float] = None, E=1.0, nu=0.3,
              Evoid=1e-6, tol=1e-12, maxit=200000):
     """dE/dtheta through the smoothed density (Eq. chain), theta = charge
-    positions, magnitudes, iso-level c and half-thickness t, for an objective
+    positions, magnitudes, mode weights alpha_hkl (Sec. 4.3), iso-level c and
+    half-thickness t, for an objective
     with dE/dC^H = dEdC (6x6):
       g_e        = dE/drho_e = sum_ij dEdC_ij (E - E_void) w_i^T Khat w_j  (self-adjoint cell problems)
       dbeta/dd   = -kappa beta (1 - beta),   dbeta/dt = +kappa beta (1 - beta)
@@ -285,6 +294,15 @@ def gradient(design, r: int, dEdC: np.ndarray, t: float, kappa: Optional[float] 
     rho = beta(d, t, kap)
     u, iters, relres, st = solve(r, rho, E, nu, Evoid, tol, maxit)
     C, _ = chom(r, rho, u, E, nu, Evoid)
+    out = gradient_backward(design, r, dEdC, t, kap, F, gF, rho, u, E, nu, Evoid)
+    out.update(C=C, u=u, rho=rho, iters=iters, relres=relres, status=st)
+    return out
+
+
+def gradient_backward(design, r: int, dEdC: np.ndarray, t: float, kap: float, F: np.ndarray, gF: np.ndarray,
+                      rho: np.ndarray, u: np.ndarray, E=1.0, nu=0.3, Evoid=1e-6):
+    """The backward half of ``gradient`` for given cell-problem solutions u of
+    the smoothed density rho = beta(d, t, kap) (Eq. chain, steps as listed there)."""
     g_e = element_sensitivity(r, u, dEdC, E, nu, Evoid)
     db = kap * rho * (1.0 - rho)            # dbeta/dt = -dbeta/dd
     dE_dd = -g_e * db
@@ -294,9 +312,9 @@ def gradient(design, r: int, dEdC: np.ndarray, t: float, kappa: Optional[float] 
     gFbar = np.zeros_like(gF)
     Fbar[ok] = dE_dd[ok] * np.sign(F[ok] - design.iso) / gn[ok]
     gFbar[ok] = (dE_dd[ok] * (-np.abs(F[ok] - design.iso) / gn[ok] ** 3))[:, None] * gF[ok]
-    g_pos, g_q = field_vjp(design, voxel_centres(r), Fbar, gFbar)
-    return dict(C=C, g_pos=g_pos, g_q=g_q, g_iso=float(-Fbar.sum()), g_t=float(np.sum(g_e * db)), u=u, rho=rho,
-                iters=iters, relres=relres, status=st, g_e=g_e)
+    g_pos, g_q, g_alpha = field_vjp(design, voxel_centres(r), Fbar, gFbar, want_alpha=True)
+    return dict(g_pos=g_pos, g_q=g_q, g_alpha=g_alpha, g_iso=float(-Fbar.sum()), g_t=float(np.sum(g_e * db)),
+                g_e=g_e)
 
 
 def isotropic_C(E=1.0, nu=0.3) -> np.ndarray:

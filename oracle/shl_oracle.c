@@ -639,18 +639,28 @@ int shlo_num_threads(void) {
  * where, for B_j(p) = sum_hkl alpha w / |n|^2 cos cos cos (charge j's basis
  * sum), F = sum_j q_j B_j, dF/dq_j = B_j, d(grad F)/dq_j = grad B_j,
  * dF/dx_j = -q_j grad B_j and d(grad F)_a/dx_jm = -q_j d_a d_m B_j (every
- * factor depends on p - p_j).  Points are split across threads; per-thread
- * partial sums are added in thread order.
+ * factor depends on p - p_j).
+ * With g_alpha (K+1)^3 given (NULL: not computed), also the mode weights of
+ * Sec. 4.3: F is linear in alpha_hkl with
+ *   dF/dalpha_hkl       = w_hkl/(h^2+k^2+l^2) sum_j q_j cos cos cos
+ *   d(grad F)/dalpha_hkl = w_hkl/(h^2+k^2+l^2) sum_j q_j grad(cos cos cos)
+ * so g_alpha[hkl] = sum_p Fbar dF/dalpha_hkl + gFbar . d(grad F)/dalpha_hkl
+ * (g_alpha[000] = 0: the constant mode is not in the truncated series).
+ * Points are split across threads; per-thread partial sums are added in
+ * thread order.
  */
 int shlo_field_vjp(int nc, const double *pos, const double *q, const double *alpha, int K, long npts,
-                   const double *pts, const double *Fbar, const double *gFbar, double *g_pos, double *g_q) {
+                   const double *pts, const double *Fbar, const double *gFbar, double *g_pos, double *g_q,
+                   double *g_alpha) {
     if (nc < 0 || K < 1 || K > 15 || npts < 0) return 1;
     const int K1 = K + 1;
     int nthr = 1;
 #ifdef _OPENMP
     nthr = omp_get_max_threads();
 #endif
-    double *acc = (double *)calloc((size_t)nthr * nc * 4, sizeof(double));
+    const int nmode = K1 * K1 * K1;
+    const size_t per_thr = (size_t)nc * 4 + (size_t)nmode;
+    double *acc = (double *)calloc((size_t)nthr * per_thr, sizeof(double));
     if (!acc) return 2;
 #pragma omp parallel
     {
@@ -658,7 +668,8 @@ int shlo_field_vjp(int nc, const double *pos, const double *q, const double *alp
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        double *my = acc + (size_t)tid * nc * 4;
+        double *my = acc + (size_t)tid * per_thr;
+        double *my_alpha = my + (size_t)nc * 4;
         double cs[3][16], sn[3][16];
 #pragma omp for schedule(static)
         for (long p = 0; p < npts; ++p) {
@@ -675,7 +686,8 @@ int shlo_field_vjp(int nc, const double *pos, const double *q, const double *alp
                         for (int l = 0; l <= K; ++l) {
                             if (h == 0 && k == 0 && l == 0) continue;
                             const double a = alpha ? alpha[(h * K1 + k) * K1 + l] : 1.0;
-                            const double coef = a * shlo_weight(h, k, l) / (double)(h * h + k * k + l * l);
+                            const double coef0 = shlo_weight(h, k, l) / (double)(h * h + k * k + l * l);
+                            const double coef = a * coef0;
                             const double w[3] = {2.0 * SHLO_PI * h, 2.0 * SHLO_PI * k, 2.0 * SHLO_PI * l};
                             const int nn[3] = {h, k, l};
                             double c[3], s[3];
@@ -683,12 +695,21 @@ int shlo_field_vjp(int nc, const double *pos, const double *q, const double *alp
                                 c[d] = cs[d][nn[d]];
                                 s[d] = sn[d][nn[d]];
                             }
-                            B += coef * c[0] * c[1] * c[2];
+                            const double bj = c[0] * c[1] * c[2];
+                            double gj[3];
+                            B += coef * bj;
                             for (int d = 0; d < 3; ++d) {
                                 double t = -w[d] * s[d];
                                 for (int e = 0; e < 3; ++e)
                                     if (e != d) t *= c[e];
+                                gj[d] = t;
                                 g[d] += coef * t;
+                            }
+                            if (g_alpha) {
+                                /* this charge's share of dE/dalpha_hkl at point p */
+                                const double *gbp = gFbar + 3 * p;
+                                my_alpha[(h * K1 + k) * K1 + l] +=
+                                    q[j] * coef0 * (Fbar[p] * bj + gbp[0] * gj[0] + gbp[1] * gj[1] + gbp[2] * gj[2]);
                             }
                             for (int d = 0; d < 3; ++d)
                                 for (int m = 0; m < 3; ++m) {
@@ -717,9 +738,15 @@ int shlo_field_vjp(int nc, const double *pos, const double *q, const double *alp
         g_q[j] = 0.0;
         g_pos[3 * j] = g_pos[3 * j + 1] = g_pos[3 * j + 2] = 0.0;
         for (int t = 0; t < nthr; ++t) {
-            const double *my = acc + (size_t)t * nc * 4;
+            const double *my = acc + (size_t)t * per_thr;
             g_q[j] += my[4 * j];
             for (int m = 0; m < 3; ++m) g_pos[3 * j + m] += my[4 * j + 1 + m];
+        }
+    }
+    if (g_alpha) {
+        for (int m = 0; m < nmode; ++m) {
+            g_alpha[m] = 0.0;
+            for (int t = 0; t < nthr; ++t) g_alpha[m] += acc[(size_t)t * per_thr + (size_t)nc * 4 + m];
         }
     }
     free(acc);

@@ -1,5 +1,8 @@
 """The GPU adjoint (shl_grad) against the oracle's adjoint, against central
 finite differences of the GPU's own C^H, and through torch.autograd."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -9,6 +12,9 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 from paper_2511_04025_b300 import inputs, shl  # noqa: E402
 from paper_2511_04025_b300.autograd import HomogenizeFn  # noqa: E402
+
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -33,14 +39,37 @@ def test_grad_matches_oracle_gradient(ctx):
     ref0 = oracle.gradient(d, r, np.zeros((6, 6)), t, tol=1e-13)
     G = 2.0 * (ref0["C"] - Ct)
     ref = oracle.gradient(d, r, G, t, tol=1e-13)
-    out = shl.shl_grad(ctx, d, r, _smooth(), G, t=t)
+    out = shl.shl_grad(ctx, d, r, _smooth(), G, t=t, want_alpha=True)
     s = np.abs(ref["C"]).max()
     assert np.max(np.abs(out["C"] - ref["C"])) <= 1e-9 * s
     scale = max(np.abs(ref["g_pos"]).max(), np.abs(ref["g_q"]).max(), abs(ref["g_iso"]), abs(ref["g_t"]))
     for k in ("g_pos", "g_q"):
         assert np.abs(out[k] - ref[k]).max() <= 1e-7 * scale, k
+    # mode weights alpha_hkl (Sec. 4.3), every entry
+    assert np.abs(out["g_alpha"] - ref["g_alpha"]).max() <= 1e-7 * np.abs(ref["g_alpha"]).max()
     assert abs(out["g_iso"] - ref["g_iso"]) <= 1e-7 * scale
     assert abs(out["g_t"] - ref["g_t"]) <= 1e-7 * scale
+
+
+@pytest.mark.parametrize("prec,tol,bound", [(shl.SHL_FP64, 1e-12, 1e-7), (shl.SHL_FP32_REFINE, 1e-10, 1e-6)])
+def test_grad_64_matches_oracle_golden(ctx, prec, tol, bound):
+    """The inverse-design gradient at full size (64^3, 24 charges +-1, 10 %
+    solid, smoothed density): GPU adjoint against the oracle's (solved to
+    1e-12) for dE/dC^H = 2 (C^H - C^T) stored with the oracle's values, every
+    parameter: positions, magnitudes, alpha, iso-level, thickness."""
+    with open(os.path.join(GOLD, "gradient64_s0.json")) as f:
+        g = json.load(f)
+    d = inputs.gradient_64(0)
+    out = shl.shl_grad(ctx, d, 64, _smooth(prec=prec, tol=tol), np.array(g["dEdC"]), t=g["t"], want_alpha=True)
+    C = np.array(g["C"])
+    assert np.abs(out["C"] - C).max() <= 1e-9 * np.abs(C).max()
+    scale = max(np.abs(g["g_pos"]).max(), np.abs(g["g_q"]).max(), abs(g["g_iso"]), abs(g["g_t"]))
+    assert np.abs(out["g_pos"] - np.array(g["g_pos"])).max() <= bound * scale
+    assert np.abs(out["g_q"] - np.array(g["g_q"])).max() <= bound * scale
+    assert abs(out["g_iso"] - g["g_iso"]) <= bound * scale
+    assert abs(out["g_t"] - g["g_t"]) <= bound * scale
+    ga = np.array(g["g_alpha"])
+    assert np.abs(out["g_alpha"] - ga).max() <= bound * np.abs(ga).max()
 
 
 def test_grad_matches_central_differences_32(ctx):

@@ -76,6 +76,58 @@ def test_adjoint_gradient_matches_finite_differences():
         return t
     checks.append((fd(muti), res["g_iso"]))
     checks.append((fd(lambda x, s: t + s), res["g_t"]))
+    # mode weights alpha_hkl (Sec. 4.3), indexed [h][k][l]
+    for idx in (1 * 16 + 0 * 4 + 0, 1 * 16 + 2 * 4 + 0, 3 * 16 + 3 * 4 + 3, 0 * 16 + 2 * 4 + 1):
+        def muta(x, s, idx=idx):
+            a = np.ones(64) if x.alpha is None else x.alpha.copy()
+            a[idx] += s
+            x.alpha = a
+            return t
+        checks.append((fd(muta), res["g_alpha"][idx]))
+    assert res["g_alpha"][0] == 0.0
     scale = max(abs(a) for a, _ in checks)
     for f, a in checks:
         assert abs(f - a) <= 1e-5 * scale + 1e-4 * abs(f), (f, a)
+
+
+def _vjp_seeds(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n), rng.standard_normal((n, 3))
+
+
+def test_field_vjp_alpha_and_q_euler_identity():
+    """F and grad F are linear in alpha and in q, so by Euler's theorem for
+    homogeneous functions of degree one
+      sum_hkl alpha_hkl dPhi/dalpha_hkl = sum_j q_j dPhi/dq_j = Phi,
+    Phi = sum_p Fbar F + gFbar . grad F, for any seeds (non-uniform alpha so a
+    wrong index order fails)."""
+    d = inputs.random_design(4, 7, 0.1, balanced=False)
+    rng = np.random.default_rng(9)
+    d.alpha = rng.uniform(0.2, 2.0, 64)
+    pts = rng.uniform(0.0, 1.0, (300, 3))
+    Fb, gFb = _vjp_seeds(300, 10)
+    F, gF = oracle.field(d, pts)
+    phi = float(Fb @ F + np.sum(gFb * gF))
+    _, g_q, g_a = oracle.field_vjp(d, pts, Fb, gFb, want_alpha=True)
+    assert abs(float(d.alpha @ g_a) - phi) <= 1e-12 * np.sum(np.abs(Fb) * np.abs(F))
+    assert abs(float(d.q @ g_q) - phi) <= 1e-12 * np.sum(np.abs(Fb) * np.abs(F))
+
+
+def test_field_vjp_alpha_matches_differences_of_the_field():
+    """dPhi/dalpha_hkl against central differences of the oracle's forward field
+    (exact up to rounding, the field being linear in alpha), every mode."""
+    d = inputs.random_design(8, 6, 0.1)
+    rng = np.random.default_rng(2)
+    d.alpha = rng.uniform(0.5, 1.5, 64)
+    pts = rng.uniform(0.0, 1.0, (64, 3))
+    Fb, gFb = _vjp_seeds(64, 3)
+    _, _, g_a = oracle.field_vjp(d, pts, Fb, gFb, want_alpha=True)
+
+    def phi(a):
+        F, gF = oracle.field(d.copy(alpha=a), pts)
+        return float(Fb @ F + np.sum(gFb * gF))
+    h = 0.25
+    fd = np.array([(phi(d.alpha + h * np.eye(64)[m]) - phi(d.alpha - h * np.eye(64)[m])) / (2 * h)
+                   for m in range(64)])
+    assert fd[0] == pytest.approx(0.0, abs=1e-12)
+    np.testing.assert_allclose(g_a, fd, rtol=0, atol=1e-10 * np.abs(fd).max())
