@@ -339,10 +339,15 @@ int shl_get_counters(shl_ctx *ctx, shl_counters *out);
  * inside the library that every GPU loading the library holds until exit.
  * It calls no cudaMalloc/cudaFree.
  *   - runs on the calling thread's current device, on stream (NULL = legacy
- *     default stream); returns without synchronising;
+ *     default stream); returns without synchronising; u_dev, C_dev and the
+ *     density must be device memory of that device (SHL_EINVAL otherwise);
  *   - 1 <= r <= 512; larger grids are rejected with SHL_EINVAL;
  *   - the first call on each device looks up the scratch address
  *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - the scratch array belongs to the device's primary context (the one the
+ *     CUDA runtime uses); the looked-up address is kept for the life of the
+ *     process, so do not call this entry point after cudaDeviceReset or from
+ *     a context created with the driver API;
  *   - all calls share the one scratch array (it keeps the last call's
  *     contents; the call clears what must start at zero), so calls whose
  *     work overlaps on the GPU (different streams, no ordering) race;

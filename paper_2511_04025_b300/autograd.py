@@ -29,7 +29,7 @@ class HomogenizeFn(torch.autograd.Function):
             setattr(o, f, getattr(opts, f))
         o.density = shl.SHL_SMOOTH
         o.warm_start = 0
-        u = torch.empty(18 * r ** 3, dtype=torch.float64, device="cuda")
+        u = torch.empty(18 * r ** 3, dtype=torch.float64, device=shl.ctx_device(handle))
         res = shl.shl_grad(handle, design, r, o, np.zeros(36), u=u)
         fctx.state = (handle, design, r, o, u)
         return torch.tensor(res["C"], dtype=torch.float64)

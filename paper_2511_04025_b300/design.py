@@ -93,7 +93,7 @@ class InverseDesign:
         E(C^H, V) with V the smoothed volume fraction of the current design."""
         t = self.thickness()
         if self._u is None:
-            self._u = torch.empty(18 * self.r ** 3, dtype=torch.float64, device="cuda")
+            self._u = torch.empty(18 * self.r ** 3, dtype=torch.float64, device=shl.ctx_device(self.h))
         for _ in range(n):
             fwd = shl.shl_grad(self.h, self.design, self.r, self.opts, np.zeros((6, 6)), u=self._u, t=t)
             _, G, gV = objectives.value_and_grad(self.fn, fwd["C"], fwd["V"])

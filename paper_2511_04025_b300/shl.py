@@ -185,17 +185,31 @@ def default_solve_opts(**kw) -> shl_solve_opts:
 # Same-name wrappers of the C entry points
 # ---------------------------------------------------------------------------
 
+_ctx_device = {}  # handle -> CUDA device ordinal it was created on
+
+
 def shl_create(device: int = 0, max_batch: int = 0, hbm_budget_bytes: int = 0) -> int:
     o = shl_opts(device=device, max_batch=max_batch, hbm_budget_bytes=hbm_budget_bytes)
     out = _vp()
     st = lib().shl_create(ctypes.byref(o), ctypes.byref(out))
     if st != SHL_OK:
         raise ShlError(st, lib().shl_last_error(None).decode())
+    _ctx_device[out.value] = device
     return out.value
 
 
 def shl_destroy(ctx: int) -> None:
+    _ctx_device.pop(ctx, None)
     lib().shl_destroy(ctx)
+
+
+def ctx_device(ctx: int):
+    """torch.device of the GPU a context (made by shl_create) runs on: buffers
+    that the context's kernels read or write must be allocated there."""
+    import torch
+    if ctx not in _ctx_device:
+        raise ValueError("ctx_device: handle was not created by shl_create in this process")
+    return torch.device("cuda", _ctx_device[ctx])
 
 
 def shl_field(ctx, design, r: int, F, gradF=None, stream=None):
@@ -267,11 +281,30 @@ def shl_homogenize_batch(ctx, designs: Sequence, rs: Sequence[int], opts: shl_so
     return C.reshape(-1, 6, 6), [s.as_dict() for s in st]
 
 
+NOALLOC_MAX_R = 512  # largest grid of shl_chom_noalloc (its fixed scratch)
+
+
 def shl_chom_noalloc(r: int, u, C_dev, mask=None, rho=None, E=1.0, nu=0.3, E_void=1e-6, stream=None):
     """C^H into the 36-double device tensor C_dev without any device allocation
-    by the library (for callers that cannot allocate); see include/shl.h."""
-    _check(None, lib().shl_chom_noalloc(r, _ptr(mask), _ptr(rho), E, nu, E_void, _ptr(u), _ptr(C_dev),
-                                        _stream(stream)))
+    by the library (for callers that cannot allocate); see include/shl.h.
+    Every tensor must sit on C_dev's device, contiguous, with its dtype and at
+    least its size (u: 18 r^3 float64; mask: r^3 uint8 or rho: r^3 float64;
+    C_dev: 36 float64); the call runs with that device current."""
+    import torch
+    # a grid size the library rejects is passed through so that it reports it
+    n = r ** 3 if 1 <= r <= NOALLOC_MAX_R else 0
+    need = [("u", u, torch.float64, 18 * n), ("C_dev", C_dev, torch.float64, 36),
+            ("mask", mask, torch.uint8, n), ("rho", rho, torch.float64, n)]
+    for name, t, dt, size in need:
+        if t is None:
+            continue
+        if not (t.is_cuda and t.device == C_dev.device):
+            raise ValueError(f"shl_chom_noalloc: {name} must be on {C_dev.device}, got {t.device}")
+        if t.dtype != dt or not t.is_contiguous() or t.numel() < size:
+            raise ValueError(f"shl_chom_noalloc: {name} must be a contiguous {dt} tensor of >= {size} elements")
+    with torch.cuda.device(C_dev.device):
+        _check(None, lib().shl_chom_noalloc(r, _ptr(mask), _ptr(rho), E, nu, E_void, _ptr(u), _ptr(C_dev),
+                                            _stream(stream)))
 
 
 def shl_grad(ctx, design, r: int, opts: shl_solve_opts, dEdC, u=None, t: Optional[float] = None,
