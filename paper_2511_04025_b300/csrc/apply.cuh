@@ -66,8 +66,35 @@ struct ApplyArgs {
     const int *active_in;  // per load-case flags when st == null (may be null)
     int case_mask;         // bit k: load case k is computed (others: output and dot left untouched)
     int vec_ok;            // p is 16-byte aligned and r is a multiple of 16 / sizeof(T)
+    unsigned *err;         // device error bits (apply_rows.cuh), or null
     ElemOp<T> op;
 };
+
+// Grid reduction of the fused dot products, run by thread 0 of the last CTA
+// with the six case totals: dot_out and, in PCG mode, alpha = rz / pq (a
+// non-positive or non-finite p.q stops that case with a numeric error).
+template <typename T>
+__device__ inline void apply_dot_finish(const ApplyArgs<T> &a, const double (&tot)[6]) {
+    if (a.dot_out)
+        for (int kk = 0; kk < 6; ++kk)
+            if ((a.case_mask >> kk) & 1) a.dot_out[kk] = tot[kk];
+    if (a.st) {
+        for (int kk = 0; kk < 6; ++kk) {
+            if (!a.st->active[kk]) continue;
+            const double pq = tot[kk];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                a.st->numeric_err = kNumErrPq;
+                a.st->active[kk] = 0;
+                a.st->alpha[kk] = 0.0;
+            } else {
+                a.st->alpha[kk] = a.st->rz[kk] / pq;
+            }
+        }
+        int na = 0;
+        for (int kk = 0; kk < 6; ++kk) na += a.st->active[kk];
+        a.st->nactive = na;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies (cp.async; completion by group)
@@ -382,27 +409,7 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
     if (!last_block_ticket(a.ticket, nblocks)) return;
     __shared__ double tot[6];
     sum_partials_ordered<6>(a.partial, nblocks, tot);
-    if (threadIdx.x == 0) {
-        if (a.dot_out)
-            for (int kk = 0; kk < 6; ++kk)
-                if ((a.case_mask >> kk) & 1) a.dot_out[kk] = tot[kk];
-        if (a.st) {
-            for (int kk = 0; kk < 6; ++kk) {
-                if (!a.st->active[kk]) continue;
-                const double pq = tot[kk];
-                if (!(pq > 0.0) || !isfinite(pq)) {
-                    a.st->numeric_err = kNumErrPq;
-                    a.st->active[kk] = 0;
-                    a.st->alpha[kk] = 0.0;
-                } else {
-                    a.st->alpha[kk] = a.st->rz[kk] / pq;
-                }
-            }
-            int na = 0;
-            for (int kk = 0; kk < 6; ++kk) na += a.st->active[kk];
-            a.st->nactive = na;
-        }
-    }
+    if (threadIdx.x == 0) apply_dot_finish(a, tot);
 }
 
 // --------------------------------------------------------------------------

@@ -1,0 +1,472 @@
+// apply_rows.cuh -- FP32 matrix-free stiffness apply q = K p (six load cases,
+// Eq. inv-design cell problems; Sec. 4.2.2: finest level on the fly, all
+// right-hand sides in one launch, converged right-hand sides skipped) for the
+// grids whose rows split evenly into warp segments: r = 32, 64, 128, 256.
+// Other grids, and the FP64 / double-float kinds, use apply_kernel
+// (apply.cuh); both compute the same operator.
+//
+// Work split.  A CTA owns one load case, TY node rows (y) over the whole
+// periodic x extent and a chunk of node planes (z).  Its threads form TY + 1
+// element rows (row 0 is the halo row just below the tile); in a row, thread
+// j holds the x-adjacent element pair (2j, 2j+1) and computes both elements
+// at once with packed FP32 pairs (one f32x2 instruction per two elements).
+// The CTA marches along z:
+//  - the node rows (and density rows) of every plane arrive by bulk
+//    asynchronous copies, one per row, issued by one warp several planes
+//    ahead into a ring of shared-memory slots; each slot has an mbarrier
+//    that counts the bytes landed;
+//  - per plane a thread transforms the top face of its two elements
+//    (Walsh-Hadamard over x and y), combines it with the bottom face kept in
+//    registers from the previous plane (z), applies the element operator in
+//    its closed form (below) scaled by the two moduli, and transforms back;
+//  - the +z half of the result is carried in registers to the next plane;
+//    the +x corner goes to the next thread of the row by a warp shuffle
+//    (the row is periodic: it wraps within the warp, or through shared
+//    memory when a row spans several warps); the +y corner row goes to the
+//    next element row through shared memory (one barrier per plane).
+// Deterministic, no atomics.
+//
+// Closed form of the transformed element blocks (element.cuh: G[c][i][j],
+// character c, components i, j).  For the isotropic hex8 element the 45
+// structural non-zeros take seven values for every Poisson ratio:
+//   G[0] = (A-B) I + B J                    (J: all ones)
+//   G[7] = D (I + J)
+//   G[1<<t]     : rows/columns t zero, the other two [[P, Q], [Q, P]]
+//   G[7^(1<<t)] : entry (t,t) = R, the other two [[F, F], [F, F]]
+// so one element and load case costs 33 multiply/adds instead of 45 (7 more
+// scale the constants by the element's modulus).  build_row_consts() reads
+// the seven values off G and checks every block against this form.
+#pragma once
+
+#include "apply.cuh"
+
+namespace shl {
+
+struct RowConsts {
+    float amb, b, p, q, f, rr, d;  // A-B, B, P, Q, F, R, D (h-scaled, E = 1)
+};
+
+// Returns the largest deviation of G from the closed form relative to
+// max |G| (round-off when the form holds).
+inline double build_row_consts(const ElemOp<double> &op, RowConsts *rc) {
+    const auto &G = op.G;
+    const double A = G[0][0][0], B = G[0][0][1], P = G[1][1][1], Q = G[1][1][2];
+    const double F = G[3][0][0], R = G[3][2][2], D = G[7][0][1];
+    double gmax = 0.0, dev = 0.0;
+    for (int c = 0; c < 8; ++c)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double want = 0.0;
+                if (c == 0) {
+                    want = i == j ? A : B;
+                } else if (c == 7) {
+                    want = i == j ? 2.0 * D : D;
+                } else if (c == 1 || c == 2 || c == 4) {
+                    const int t = c == 1 ? 0 : (c == 2 ? 1 : 2);
+                    want = (i == t || j == t) ? 0.0 : (i == j ? P : Q);
+                } else {
+                    const int t = c == 6 ? 0 : (c == 5 ? 1 : 2);
+                    want = (i == t && j == t) ? R : ((i == t || j == t) ? 0.0 : F);
+                }
+                gmax = std::fmax(gmax, std::fabs(G[c][i][j]));
+                dev = std::fmax(dev, std::fabs(G[c][i][j] - want));
+            }
+    rc->amb = (float)(A - B);
+    rc->b = (float)B;
+    rc->p = (float)P;
+    rc->q = (float)Q;
+    rc->f = (float)F;
+    rc->rr = (float)R;
+    rc->d = (float)D;
+    return gmax > 0.0 ? dev / gmax : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (f32x2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+__device__ __forceinline__ float2 p2splat(float v) { return make_float2(v, v); }
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk asynchronous copies (shared-memory addresses as u32)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false after `limit` unsuccessful polls (each poll itself
+// blocks for a hardware-defined while), so a copy that never lands cannot
+// hang the kernel.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned limit = 1u << 22) {
+    for (unsigned it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+// Error bits of the row apply (ApplyArgs::err).
+constexpr unsigned kApplyErrWaitTimeout = 1u;
+
+// ---------------------------------------------------------------------------
+// Shape of one CTA
+// ---------------------------------------------------------------------------
+template <int R>
+struct RowShape {
+    static_assert(R == 32 || R == 64 || R == 128 || R == 256, "row apply: r must be 32, 64, 128 or 256");
+    // output node rows per CTA: the warps of a CTA spread over the SM's four
+    // schedulers, whose register files bound the registers per thread; these
+    // heights keep every instantiation at <= 3 warps per scheduler (<= 168
+    // registers, no spills)
+    static constexpr int TY = R <= 64 ? 8 : (R == 128 ? 4 : 2);
+    static constexpr int P = R / 2;                // element pairs (threads) per row
+    static constexpr int NR = TY + 1;              // element rows, row 0 = halo
+    static constexpr int NYR = TY + 2;             // node rows per plane
+    static constexpr int LIVE = NR * P;            // threads with an element pair
+    static constexpr int THREADS = (LIVE + 31) / 32 * 32;
+    static constexpr int S = P > 32 ? P / 32 : 1;  // warps per row
+    static constexpr int PD = 3;                   // planes copied ahead of use
+    static constexpr int NSLOT = PD + 1;           // ring slots
+    static constexpr int NODE_BYTES = 3 * NYR * R * 4;
+    template <bool SMOOTH>
+    __host__ __device__ static constexpr int den_bytes() { return NR * R * (SMOOTH ? 8 : 1); }
+    template <bool SMOOTH>
+    __host__ __device__ static constexpr int slot_bytes() { return (NODE_BYTES + den_bytes<SMOOTH>() + 127) / 128 * 128; }
+    template <bool SMOOTH>
+    __host__ __device__ static constexpr int copy_bytes() { return NODE_BYTES + den_bytes<SMOOTH>(); }
+    static constexpr int YTOP_FLOATS = 2 * NR * 3 * R;
+    static constexpr int SPILL_FLOATS = S > 1 ? 2 * NR * S * 6 : 0;
+    template <bool SMOOTH>
+    __host__ __device__ static constexpr size_t smem() {
+        return (size_t)NSLOT * slot_bytes<SMOOTH>() + sizeof(float) * (YTOP_FLOATS + SPILL_FLOATS) + 8 * NSLOT;
+    }
+};
+
+// Density of one element pair -> its two moduli (EA, EB).
+template <bool SMOOTH>
+__device__ __forceinline__ float2 pair_modulus(const unsigned char *den_row, int x, float E, float Ev) {
+    if constexpr (SMOOTH) {
+        const double2 rho = *reinterpret_cast<const double2 *>(den_row + (size_t)x * 8);
+        const float2 rf = make_float2(__double2float_rn(rho.x), __double2float_rn(rho.y));
+        return p2fma(rf, p2splat(E - Ev), p2splat(Ev));
+    } else {
+        const unsigned m = *reinterpret_cast<const unsigned short *>(den_row + x);
+        return make_float2((m & 0xffu) ? E : Ev, (m >> 8) ? E : Ev);
+    }
+}
+
+template <int R, bool SMOOTH>
+__global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
+    apply_rows_kernel(const ApplyArgs<float> a, const RowConsts kc) {
+    pdl_enter();
+    using Sh = RowShape<R>;
+    constexpr int TY = Sh::TY, P = Sh::P, NR = Sh::NR, NYR = Sh::NYR, S = Sh::S, PD = Sh::PD, NSLOT = Sh::NSLOT;
+    constexpr int SLOT = Sh::template slot_bytes<SMOOTH>();
+    constexpr int DEN_ROW = R * (SMOOTH ? 8 : 1);
+    extern __shared__ __align__(16) unsigned char rows_smem[];  // 16-byte aligned: bulk-copy destinations
+    unsigned char *const smraw = rows_smem;
+    float *ytop = reinterpret_cast<float *>(smraw + (size_t)NSLOT * SLOT);  // [2][NR][3][R]
+    float *spill = ytop + Sh::YTOP_FLOATS;                                  // [2][NR][S][2][3]
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(spill + Sh::SPILL_FLOATS);
+
+    if (a.st && a.st->nactive == 0) return;  // uniform: the solve has finished
+    const int k = blockIdx.z;
+    bool act = k < a.nvec;
+    if (act && a.st) act = a.st->active[k] != 0;
+    if (act && a.active_in) act = a.active_in[k] != 0;
+    act = act && ((a.case_mask >> k) & 1);
+    // packed compensated sum of this thread's p.q (or q.q)
+    float2 ds = make_float2(0.f, 0.f), dc = make_float2(0.f, 0.f);
+
+    if (act) {
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        const bool live = tid < Sh::LIVE;
+        const int i = live ? tid / P : NR - 1;  // element row (idle threads shadow the last row, write nothing)
+        const int jp = live ? tid % P : 0;      // element pair
+        const int x = 2 * jp;
+        const int xn = (x + 2) & (R - 1);       // node x + 2, periodic
+        const int seg = jp / 32;
+        const size_t N = (size_t)R * R * R;
+        const int y0 = blockIdx.x * TY;
+        const int z0 = (int)(blockIdx.y * R) / a.zc, tz = (int)((blockIdx.y + 1) * R) / a.zc - z0;
+        const float *pk = a.p + (size_t)(3 * k) * N;
+        const unsigned char *den = SMOOTH ? reinterpret_cast<const unsigned char *>(a.rho) : a.mask;
+        const unsigned smem0 = smem_u32(smraw);
+        const unsigned bar0 = smem_u32(mbar);
+
+        if (tid == 0) {
+            for (int b = 0; b < NSLOT; ++b) mbar_init(bar0 + 8 * b, 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+
+        // plane t of the chunk = node plane z0 - 1 + t (and its element plane's density rows)
+        auto issue = [&](int t) {
+            if (t > tz + 1) return;
+            const int slot = t % NSLOT;
+            const unsigned bar = bar0 + 8 * slot;
+            const unsigned dst0 = smem0 + slot * SLOT;
+            const int zt = wrapi(z0 - 1 + t, R);
+            // The slot's previous plane was last read through the generic proxy
+            // before the previous step's barrier, and every value read was
+            // consumed into registers before that barrier, so no read can still
+            // be pending when the copy overwrites the slot (no proxy fence: it
+            // would also wait for this thread's outstanding global stores).
+            if (lane == 0) mbar_expect_tx(bar, (unsigned)Sh::template copy_bytes<SMOOTH>());
+            __syncwarp();
+            // The NYR node rows y0 - 1 .. y0 + TY of a component are contiguous
+            // in memory except across the periodic wrap, so each component takes
+            // one copy (two at the first and last tile), likewise the NR density
+            // rows: at most 8 copies per plane, lanes 0..7.
+            const int ys = wrapi(y0 - 1, R);
+            const int n1 = ys + NYR <= R ? NYR : R - ys;  // node rows before the wrap
+            const int d1 = ys + NR <= R ? NR : R - ys;    // density rows before the wrap
+            if (lane < 8) {
+                const int c = lane >> 1, part = lane & 1;
+                if (c < 3) {
+                    const int rows = part ? NYR - n1 : n1;
+                    const int yg = part ? 0 : ys;     // first global row of the run
+                    const int jj = part ? n1 : 0;     // first slot row of the run
+                    if (rows > 0)
+                        bulk_g2s(dst0 + (c * NYR + jj) * R * 4, pk + (size_t)c * N + ((size_t)zt * R + yg) * R,
+                                 rows * R * 4, bar);
+                } else {
+                    const int rows = part ? NR - d1 : d1;
+                    const int yg = part ? 0 : ys;
+                    const int ii = part ? d1 : 0;
+                    if (rows > 0)
+                        bulk_g2s(dst0 + Sh::NODE_BYTES + ii * DEN_ROW,
+                                 den + ((size_t)zt * R + yg) * (size_t)DEN_ROW, rows * DEN_ROW, bar);
+                }
+            }
+        };
+        bool wait_ok = true;
+        auto wait_plane = [&](int t) {
+            const int slot = t % NSLOT;
+            if (!mbar_wait_bounded(bar0 + 8 * slot, (unsigned)((t / NSLOT) & 1))) wait_ok = false;
+        };
+
+        // top face of plane t: Walsh-Hadamard over x, y of both elements' faces;
+        // own = p at the pair's own nodes (x, x + 1) of node row i
+        auto face = [&](int t, float2 (&ft)[3][4], float2 (&own)[3]) {
+            const float *sb = reinterpret_cast<const float *>(smraw + (t % NSLOT) * SLOT);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *rb = sb + (c * NYR + i) * R;
+                const float *rt = rb + R;
+                const float2 b0 = *reinterpret_cast<const float2 *>(rb + x);
+                const float b1 = rb[xn];
+                const float2 t0 = *reinterpret_cast<const float2 *>(rt + x);
+                const float t1 = rt[xn];
+                own[c] = b0;
+                const float2 a10 = make_float2(b0.y, b1), a11 = make_float2(t0.y, t1);
+                const float2 s0 = p2add(b0, a10), d0 = p2sub(b0, a10);
+                const float2 s1 = p2add(t0, a11), d1 = p2sub(t0, a11);
+                ft[c][0] = p2add(s0, s1);
+                ft[c][1] = p2add(d0, d1);
+                ft[c][2] = p2sub(s0, s1);
+                ft[c][3] = p2sub(d0, d1);
+            }
+        };
+
+        // prologue: the first planes in flight, the bottom face of element plane z0 - 1
+        if (warp == 0)
+#pragma unroll 1
+            for (int t = 0; t < PD; ++t) issue(t);
+        float2 ftb[3][4], carry[3][4], own_b[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) carry[c][j] = make_float2(0.f, 0.f);
+        wait_plane(0);
+        face(0, ftb, own_b);
+
+        const float2 kA = p2splat(kc.amb), kB = p2splat(kc.b), kP = p2splat(kc.p), kQ = p2splat(kc.q),
+                     kF = p2splat(kc.f), kR = p2splat(kc.rr), kD = p2splat(kc.d);
+        const int src_lane = P >= 32 ? ((lane + 31) & 31) : ((lane & ~(P - 1)) | ((lane + P - 1) & (P - 1)));
+        const bool patch = (S > 1) && live && (lane == 0);  // the row's left neighbour is in another warp
+        const int segm1 = (seg + S - 1) % S;
+
+#pragma unroll 1
+        for (int s = 0; s <= tz; ++s) {
+            if (warp == 0) issue(s + PD);
+            wait_plane(s + 1);
+            // moduli of element plane z0 - 1 + s (density rows of plane s)
+            const float2 Ee = pair_modulus<SMOOTH>(smraw + (s % NSLOT) * SLOT + Sh::NODE_BYTES + i * DEN_ROW, x,
+                                                   a.E, a.Evoid);
+            float2 ftt[3][4], own_t[3];
+            face(s + 1, ftt, own_t);
+            // transformed element displacements u[c][m] (mode m = x + 2y + 4z bits)
+            float2 u[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                for (int j = 1; j < 4; ++j) u[c][j] = p2add(ftb[c][j], ftt[c][j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[c][j + 4] = p2sub(ftb[c][j], ftt[c][j]);
+            }
+            // y = E G u in the closed form (the translation modes u[c][0] and
+            // y[c][0] are zero)
+            const float2 eA = p2mul(Ee, kA), eB = p2mul(Ee, kB), eP = p2mul(Ee, kP), eQ = p2mul(Ee, kQ),
+                         eF = p2mul(Ee, kF), eR = p2mul(Ee, kR), eD = p2mul(Ee, kD);
+            float2 y[3][8];
+            {  // c = 0: (u01, u12, u24) -> (y01, y12, y24)
+                const float2 t0 = p2mul(eB, p2add(p2add(u[0][1], u[1][2]), u[2][4]));
+                y[0][1] = p2fma(eA, u[0][1], t0);
+                y[1][2] = p2fma(eA, u[1][2], t0);
+                y[2][4] = p2fma(eA, u[2][4], t0);
+            }
+            {  // c = 7: (u06, u15, u23)
+                const float2 t7 = p2mul(eD, p2add(p2add(u[0][6], u[1][5]), u[2][3]));
+                y[0][6] = p2fma(eD, u[0][6], t7);
+                y[1][5] = p2fma(eD, u[1][5], t7);
+                y[2][3] = p2fma(eD, u[2][3], t7);
+            }
+            // c = 1 (t = 0): (u13, u25); c = 2 (t = 1): (u03, u26); c = 4 (t = 2): (u05, u16)
+            y[1][3] = p2fma(eP, u[1][3], p2mul(eQ, u[2][5]));
+            y[2][5] = p2fma(eP, u[2][5], p2mul(eQ, u[1][3]));
+            y[0][3] = p2fma(eP, u[0][3], p2mul(eQ, u[2][6]));
+            y[2][6] = p2fma(eP, u[2][6], p2mul(eQ, u[0][3]));
+            y[0][5] = p2fma(eP, u[0][5], p2mul(eQ, u[1][6]));
+            y[1][6] = p2fma(eP, u[1][6], p2mul(eQ, u[0][5]));
+            // c = 6 (t = 0): u07 -> y07, (u14, u22) -> y14 = y22; c = 5 (t = 1): u17, (u04, u21);
+            // c = 3 (t = 2): u27, (u02, u11)
+            y[0][7] = p2mul(eR, u[0][7]);
+            y[1][4] = y[2][2] = p2mul(eF, p2add(u[1][4], u[2][2]));
+            y[1][7] = p2mul(eR, u[1][7]);
+            y[0][4] = y[2][1] = p2mul(eF, p2add(u[0][4], u[2][1]));
+            y[2][7] = p2mul(eR, u[2][7]);
+            y[0][2] = y[1][1] = p2mul(eF, p2add(u[0][2], u[1][1]));
+
+            // back to corners: z split (bottom face = node plane z0 - 1 + s,
+            // top face carried), then x, y.  W[c][b]: corner b = bx + 2 by of
+            // both elements (packed).
+            float2 W[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float2 F[4];
+                F[0] = p2sub(y[c][4], carry[c][0]);  // carry[c][0] holds -(top of mode 0) = y_prev[c][4]
+                carry[c][0] = y[c][4];
+#pragma unroll
+                for (int j = 1; j < 4; ++j) {
+                    F[j] = p2add(carry[c][j], p2add(y[c][j], y[c][j + 4]));
+                    carry[c][j] = p2sub(y[c][j], y[c][j + 4]);
+                }
+                const float2 t0 = p2add(F[0], F[1]), t1 = p2sub(F[0], F[1]), t2 = p2add(F[2], F[3]),
+                             t3 = p2sub(F[2], F[3]);
+                W[c][0] = p2add(t0, t2);
+                W[c][1] = p2add(t1, t3);
+                W[c][2] = p2sub(t0, t2);
+                W[c][3] = p2sub(t1, t3);
+            }
+            // x exchange: node x gets the +x corner of the left neighbour's second element
+            float rb1[3], rb3[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                rb1[c] = __shfl_sync(0xffffffffu, W[c][1].y, src_lane);
+                rb3[c] = __shfl_sync(0xffffffffu, W[c][3].y, src_lane);
+            }
+            // top-row partial for the next element row (node row i + 1)
+            const int par = s & 1;
+            float *yt = ytop + ((size_t)(par * NR + i) * 3) * R;
+            if (live) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 ot = p2add(W[c][2], make_float2(patch ? 0.f : rb3[c], W[c][3].x));
+                    *reinterpret_cast<float2 *>(yt + c * R + x) = ot;
+                }
+                if (S > 1 && lane == 31) {
+                    float *sp = spill + ((size_t)((par * NR + i) * S + seg) * 2) * 3;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        sp[c] = W[c][1].y;
+                        sp[3 + c] = W[c][3].y;
+                    }
+                }
+            }
+            __syncthreads();
+            const int ez = z0 - 1 + s;
+            if (s >= 1 && live && i >= 1) {
+                const float *ytp = ytop + ((size_t)(par * NR + i - 1) * 3) * R;
+                const float *spb = spill + ((size_t)((par * NR + i) * S + segm1) * 2) * 3;      // own row, left warp
+                const float *spt = spill + ((size_t)((par * NR + i - 1) * S + segm1) * 2) * 3;  // row below, left warp
+                const int ny = y0 - 1 + i;  // node row (inside the tile: 0 <= ny - y0 < TY)
+                const size_t nrow = ((size_t)ez * R + ny) * R + x;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float2 otp = *reinterpret_cast<const float2 *>(ytp + c * R + x);
+                    float recv1 = rb1[c];
+                    if (patch) {
+                        recv1 = spb[c];
+                        otp.x += spt[3 + c];
+                    }
+                    float2 qv = p2add(p2add(W[c][0], make_float2(recv1, W[c][1].x)), otp);
+                    if (a.pin && nrow == 0) qv.x = 0.f;
+                    *reinterpret_cast<float2 *>(a.q + (size_t)(3 * k + c) * N + nrow) = qv;
+                    if (a.dot) {  // packed compensated sum
+                        const float2 v = a.dot == 1 ? p2mul(qv, own_b[c]) : p2mul(qv, qv);
+                        const float2 yv = p2sub(v, dc);
+                        const float2 tv = p2add(ds, yv);
+                        dc = p2sub(p2sub(tv, ds), yv);
+                        ds = tv;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                own_b[c] = own_t[c];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ftb[c][j] = ftt[c][j];
+            }
+        }
+        if (!wait_ok && a.err) atomicOr(a.err, kApplyErrWaitTimeout);
+        // every plane issued was waited for in the loop; nothing is in flight
+    }
+
+    if (!a.dot) return;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    // this thread's two compensated halves as one double-float, then the CTA's
+    // row: its own case's sum in column k, zeros elsewhere
+    const float2 v[1] = {df_add(two_sum(ds.x, -dc.x), two_sum(ds.y, -dc.y))};
+    double sum[1];
+    block_sum_df<1>(v, sum);
+    if (threadIdx.x < 6) a.partial[(size_t)bid * 6 + threadIdx.x] = threadIdx.x == (unsigned)k ? sum[0] : 0.0;
+    if (a.defer) return;  // the consumer reduces the per-CTA partials itself
+    if (!last_block_ticket(a.ticket, nblocks)) return;
+    __shared__ double tot[6];
+    sum_partials_ordered<6>(a.partial, nblocks, tot);
+    if (threadIdx.x == 0) apply_dot_finish(a, tot);
+}
+
+}  // namespace shl

@@ -1,5 +1,6 @@
 // shl.cu -- libshl C-ABI entry points (include/shl.h) and the host drivers of
 // the solve.  One translation unit for the whole library.
+#include "apply_rows.cuh"
 #include "chom.cuh"
 #include "common.cuh"
 #include "element.cuh"
@@ -106,13 +107,155 @@ inline int apply_zc(int r, int nvec) {
     return pick_zc(r, nvec, sizeof(T) == 4 ? 2 : 1);
 }
 
+// ---------------------------------------------------------------------------
+// Row apply (apply_rows.cuh): FP32, r = 32, 64, 128, 256
+// ---------------------------------------------------------------------------
+inline bool rows_grid(int r) { return r == 32 || r == 64 || r == 128 || r == 256; }
+inline int rows_ty(int r) { return r <= 64 ? 8 : (r == 128 ? 4 : 2); }
+
+// Shared-memory opt-in and resident CTAs per SM of one row-apply kernel on
+// the current device (queried once per device).
+template <int R, bool SMOOTH>
+inline int rows_prepare() {
+    static std::mutex mu;
+    static int occ[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    std::lock_guard<std::mutex> lk(mu);
+    if (occ[dev] == 0) {
+        const size_t sm = RowShape<R>::template smem<SMOOTH>();
+        int n = 0;
+        if (cudaFuncSetAttribute(apply_rows_kernel<R, SMOOTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_rows_kernel<R, SMOOTH>, RowShape<R>::THREADS,
+                                                          sm) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        occ[dev] = n > 0 ? n : -1;
+    }
+    return occ[dev];
+}
+inline int rows_occupancy(int r, bool smooth) {
+    switch (r) {
+        case 32: return smooth ? rows_prepare<32, true>() : rows_prepare<32, false>();
+        case 64: return smooth ? rows_prepare<64, true>() : rows_prepare<64, false>();
+        case 128: return smooth ? rows_prepare<128, true>() : rows_prepare<128, false>();
+        case 256: return smooth ? rows_prepare<256, true>() : rows_prepare<256, false>();
+    }
+    return -1;
+}
+// z chunks of the row apply: the same makespan model as pick_zc over
+// r / TY row tiles per load case.
+inline int pick_zc_rows(int r, int nvec, int ctas_per_sm) {
+    const long long nxy = (long long)(r / rows_ty(r)) * nvec;
+    const long long slots = 148LL * ctas_per_sm;
+    int best = 1;
+    long long best_cost = -1;
+    for (int zc = 1; zc <= r && zc <= 128; ++zc) {
+        const long long h = (r + zc - 1) / zc;
+        const long long cost = ((nxy * zc + slots - 1) / slots) * (h + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best = zc;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+// Launch geometry of the apply for grid r, nvec load cases and a density
+// buffer: the row kernel when it serves this grid (FP32, r = 32..256, density
+// rows 16-byte aligned for the bulk copies), else the tile kernel.  The
+// deferred p.q partials are laid out by it (gx * gy rows per load case).
+struct ApplyGeom {
+    int gx, gy, rows;
+};
+template <typename T>
+inline ApplyGeom apply_geom(int r, int nvec, const uint8_t *mask, const double *rho) {
+    const void *den = rho ? (const void *)rho : (const void *)mask;
+    if (std::is_same<T, float>::value && rows_grid(r) && den && (reinterpret_cast<uintptr_t>(den) & 15) == 0) {
+        const int occ = rows_occupancy(r, rho != nullptr);
+        if (occ > 0) return ApplyGeom{r / rows_ty(r), pick_zc_rows(r, nvec, occ), 1};
+    }
+    return ApplyGeom{((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY), apply_zc<T>(r, nvec), 0};
+}
+
+template <typename T>
+inline int launch_apply_rows(shl_ctx *ctx, ApplyArgs<T> a, const ApplyGeom &geo, cudaStream_t s) {
+    if constexpr (!std::is_same<T, float>::value) {
+        return set_err(ctx, SHL_EINVAL, "internal: row apply is FP32 only");
+    } else {
+        RowConsts kc;
+        double dev = 0.0;
+        {
+            ElemOp<double> od;
+            for (int c = 0; c < 8; ++c)
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) od.G[c][i][j] = (double)a.op.G[c][i][j];
+            dev = build_row_consts(od, &kc);
+        }
+        if (!(dev < 1e-5)) return set_err(ctx, SHL_EINVAL, "element blocks off their closed form (%g)", dev);
+        if (!a.err) SHL_TRY(ws_get_t(ctx, "apply_err", 1, &a.err));
+        a.zc = geo.gy;
+        const dim3 g(geo.gx, geo.gy, a.nvec);
+        const bool sm = a.rho != nullptr;
+        switch (a.r) {
+            case 32:
+                if (sm) pdl_launch(apply_rows_kernel<32, true>, g, RowShape<32>::THREADS, RowShape<32>::smem<true>(), s, a, kc);
+                else pdl_launch(apply_rows_kernel<32, false>, g, RowShape<32>::THREADS, RowShape<32>::smem<false>(), s, a, kc);
+                break;
+            case 64:
+                if (sm) pdl_launch(apply_rows_kernel<64, true>, g, RowShape<64>::THREADS, RowShape<64>::smem<true>(), s, a, kc);
+                else pdl_launch(apply_rows_kernel<64, false>, g, RowShape<64>::THREADS, RowShape<64>::smem<false>(), s, a, kc);
+                break;
+            case 128:
+                if (sm) pdl_launch(apply_rows_kernel<128, true>, g, RowShape<128>::THREADS, RowShape<128>::smem<true>(), s, a, kc);
+                else pdl_launch(apply_rows_kernel<128, false>, g, RowShape<128>::THREADS, RowShape<128>::smem<false>(), s, a, kc);
+                break;
+            case 256:
+                if (sm) pdl_launch(apply_rows_kernel<256, true>, g, RowShape<256>::THREADS, RowShape<256>::smem<true>(), s, a, kc);
+                else pdl_launch(apply_rows_kernel<256, false>, g, RowShape<256>::THREADS, RowShape<256>::smem<false>(), s, a, kc);
+                break;
+            default:
+                return set_err(ctx, SHL_EINVAL, "internal: row apply for r=%d", a.r);
+        }
+        ++ctx->launches;
+        SHL_CUDA(ctx, cudaGetLastError());
+        return SHL_OK;
+    }
+}
+
 template <typename T>
 int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
     using S = ApplyShape<T, kTX, kTY>;
+    ApplyGeom geo = apply_geom<T>(a.r, a.nvec, a.mask, a.rho);
+    if (geo.rows) {
+        // the bulk row copies need 16-byte aligned rows of p, the paired stores 8-byte aligned q
+        const bool ok = !a.resid && a.p && (reinterpret_cast<uintptr_t>(a.p) & 15) == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.q) & 7) == 0;
+        if (!ok && a.dot && a.defer)
+            return set_err(ctx, SHL_EINVAL, "internal: deferred apply partials need aligned p and q");
+        if (ok) {
+            if (a.dot) {
+                if (!a.partial) {
+                    double *partial = nullptr;
+                    SHL_TRY(ws_get_t(ctx, "apply_partial", (size_t)geo.gx * geo.gy * a.nvec * 6, &partial));
+                    a.partial = partial;
+                }
+                if (!a.ticket) {
+                    unsigned *ticket = nullptr;
+                    SHL_TRY(ws_get_t(ctx, "apply_ticket", 1, &ticket));
+                    a.ticket = ticket;
+                }
+            }
+            return launch_apply_rows<T>(ctx, a, geo, s);
+        }
+        geo = ApplyGeom{((a.r + kTX - 1) / kTX) * ((a.r + kTY - 1) / kTY), apply_zc<T>(a.r, a.nvec), 0};
+    }
     apply_smem_attr<T>();
-    a.zc = apply_zc<T>(a.r, a.nvec);
-    const int tiles = ((a.r + kTX - 1) / kTX) * ((a.r + kTY - 1) / kTY);
-    const dim3 g(tiles, a.zc, a.nvec);
+    a.zc = geo.gy;
+    const dim3 g(geo.gx, a.zc, a.nvec);
     a.vec_ok = (a.r % S::VEC == 0) && ((reinterpret_cast<uintptr_t>(a.p) & 15) == 0);
     if (a.dot) {
         if (!a.partial) {
@@ -445,8 +588,9 @@ inline void launch_vec_update(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom 
 
 // Apply grid CTAs per load case (the deferred p.q partials of one case).
 template <typename T>
-inline int apply_ctas_per_case(int r) {
-    return ((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<T>(r, 6);
+inline int apply_ctas_per_case(int r, const Density &den) {
+    const ApplyGeom g = apply_geom<T>(r, 6, den.mask, den.rho);
+    return g.gx * g.gy;
 }
 
 template <typename T>
@@ -489,7 +633,7 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     a.ticket = &st->ticket_apply;
     const int chunk = 32;
     {
-        const size_t nblk = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<T>(r, 6) * 6;
+        const size_t nblk = (size_t)apply_ctas_per_case<T>(r, den) * 6;
         double *ap = nullptr;
         SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
         a.partial = ap;
@@ -498,7 +642,8 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     IterGraph graph;
     SHL_TRY(capture_iteration(ctx, s, &graph, [&]() -> int {
         SHL_TRY(launch_apply<T>(ctx, a, s));
-        launch_vec_update<T>(ctx, va, vg, FineJacobi{}, false, ApplyDot{a.partial, apply_ctas_per_case<T>(r)}, s);
+        launch_vec_update<T>(ctx, va, vg, FineJacobi{}, false, ApplyDot{a.partial, apply_ctas_per_case<T>(r, den)},
+                             s);
         launch_vec_direction<T>(ctx, va, vg, s);
         return SHL_OK;
     }));
@@ -1085,8 +1230,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             const int chunk = use_mg ? 8 : 32;
             // workspaces the iteration uses must exist before capture
             {
-                const size_t nblk =
-                    (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<float>(r, 6) * 6;
+                const size_t nblk = (size_t)apply_ctas_per_case<float>(r, den) * 6;
                 double *ap = nullptr;
                 SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
                 a.partial = ap;
@@ -1099,7 +1243,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             if (use_mg) fj = FineJacobi{mg.lv[0].Dinv, mg.lv[0].omega, z32};
             auto iteration = [&]() -> int {
                 SHL_TRY(launch_apply<float>(ctx, a, s));
-                launch_vec_update<float>(ctx, va, vg, fj, use_mg, ApplyDot{a.partial, apply_ctas_per_case<float>(r)},
+                launch_vec_update<float>(ctx, va, vg, fj, use_mg, ApplyDot{a.partial, apply_ctas_per_case<float>(r, den)},
                                          s);
                 if (use_mg) {
                     SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s, kVcFirstFused | kVcLastExternal));
@@ -1172,7 +1316,15 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
     if (out->status == SHL_ENUMERIC) SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, 0x3f, opdf));
     double hn[24];
     SHL_CUDA(ctx, cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s));
+    unsigned *aerr = nullptr, haerr = 0;
+    SHL_TRY(ws_get_t(ctx, "apply_err", 1, &aerr));
+    SHL_CUDA(ctx, cudaMemcpyAsync(&haerr, aerr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    if (haerr) {
+        SHL_CUDA(ctx, cudaMemsetAsync(aerr, 0, sizeof(unsigned), s));
+        return set_err(ctx, SHL_ECUDA, "stiffness apply: a bulk row copy did not complete in time (error bits %#x)",
+                       haerr);
+    }
     for (int k = 0; k < 6; ++k) {
         out->relres[k] = hn[k] > 0.0 ? std::sqrt(hn[12 + k] / hn[k]) : std::sqrt(hn[12 + k]);
         if (!std::isfinite(out->relres[k]))
@@ -1787,6 +1939,25 @@ extern "C" int shl_chom_noalloc(int32_t r, const uint8_t *mask_dev, const double
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_err(nullptr, SHL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    // the kernel runs on the current device: buffers of another device (or
+    // host memory) would be read and written through the wrong address space
+    const void *bufs[4] = {u_dev, C_dev, mask_dev, rho_dev};
+    const char *names[4] = {"u_dev", "C_dev", "mask_dev", "rho_dev"};
+    for (int i = 0; i < 4; ++i) {
+        if (!bufs[i]) continue;
+        cudaPointerAttributes at{};
+        e = cudaPointerGetAttributes(&at, bufs[i]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(nullptr, SHL_EINVAL, "shl_chom_noalloc: %s is not a CUDA pointer (%s)", names[i],
+                           cudaGetErrorString(e));
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+            return set_err(nullptr, SHL_EINVAL, "shl_chom_noalloc: %s is not device memory", names[i]);
+        if (at.device != dev)
+            return set_err(nullptr, SHL_EINVAL, "shl_chom_noalloc: %s is on device %d, the current device is %d",
+                           names[i], at.device, dev);
+    }
     unsigned char *scratch = nullptr;
     SHL_TRY(noalloc_scratch(dev, &scratch));
     ElemOp<double> op;
