@@ -44,10 +44,12 @@ WORKLOADS = {
 }
 APPLY_BYTES_PER_NODE_F32 = 72 + 72 + 1  # read p (18 floats), write q (18 floats), 1 mask byte
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per launch of the FP32 stiffness apply at 64^3,
-# from one `ncu --set full` capture of `bench.py --kernel apply --r 64`; reset
-# to None whenever the kernel changes.
-APPLY_TRAFFIC_64 = 19_192_576
+# DRAM bytes (read + write) per launch of the FP32 stiffness apply at 64^3
+# (the row kernel), from one `ncu --set full` capture of
+# `bench.py --kernel apply --r 64`: reads 19,190,272 B (p and the mask, the
+# algorithmic minimum); q's writes were still in L2 when the captured launch
+# ended (0 B written).  Reset to None whenever the kernel changes.
+APPLY_TRAFFIC_64 = 19_190_272
 
 
 def peaks():
@@ -135,6 +137,22 @@ def oracle_sample(design, r, golden_iters):
     sample = (f"oracle on one {r}^3 design: field+voxelise, assembly, {n_s} PCG iterations and C^H timed; "
               f"iterations scaled to {golden_iters} (the oracle's own count to 1e-12 on the seed-0 design)")
     return 1.0 / per_design, per_design, sample, oracle.num_threads()
+
+
+def oracle_validate():
+    """One fully converged oracle solve (32^3, 8 charges, 15 % solid, to
+    1e-12), timed whole, beside the sample model's prediction for the same
+    design (the model times 60 iterations and scales by the iteration count):
+    the ratio measured / predicted checks the scaling the baseline rests on."""
+    import oracle
+    from paper_2511_04025_b300 import inputs
+    d, r = inputs.plain_32(0), 32
+    t0 = time.perf_counter()
+    res = oracle.homogenize(d, r, tol=1e-12)
+    full = time.perf_counter() - t0
+    _, predicted, _, cores = oracle_sample(d, r, int(max(res["iters"])))
+    return {"design": "plain_32 seed 0 (32^3)", "iters": int(max(res["iters"])), "measured_s": full,
+            "predicted_s": predicted, "ratio": full / predicted, "cores": cores}
 
 
 def golden_iters(workload):
@@ -227,7 +245,7 @@ def apply_roofline(r, apply_s):
     peak, peak_kind = peaks()
     achieved = APPLY_BYTES_PER_NODE_F32 * r ** 3 / apply_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": "apply_kernel<float> (stiffness apply)",
+            "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": "apply_rows_kernel<64> (FP32 stiffness apply)" if r in (32, 64, 128, 256) else "apply_kernel<float> (FP32 stiffness apply)",
             "peak_kind": peak_kind, "launch_us": apply_s * 1e6, "operands": "HBM (rotating > L2)"}
 
 
@@ -414,6 +432,83 @@ def run_design(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_cubic128(h, stream, flush, opts, n=3):
+    """128^3 O_h designs (48 charges, 5 % solid) one at a time, CUDA events on
+    the launch stream with L2 flushed between designs; C^H of seed 0 against
+    the oracle's stored 128^3 value (tests/golden, solved to 1e-11) and the
+    cubic symmetry of every C^H."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    r = 128
+    designs = [inputs.cubic_128(s) for s in range(n + 1)]
+    shl.shl_homogenize(h, designs[n], r, opts, stream=stream)  # warm-up (graphs, workspaces)
+    ms, Cs, its = [], [], []
+    for d in designs[:n]:
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C, st = shl.shl_homogenize(h, d, r, opts, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        Cs.append(C)
+        its.append(max(st["iters"]))
+    out = {"designs_per_s": n / (sum(ms) / 1e3), "ms_per_design": float(np.mean(ms)), "designs": n,
+           "iters_max": its, "cubic_symmetry_err_max": max(cubic_symmetry_err(C) for C in Cs)}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "cubic128_s0.json")) as f:
+            g = np.array(json.load(f)["C"])
+        out["chom_entry_err_vs_oracle"] = float(np.max(np.abs(Cs[0] - g) / np.maximum(np.abs(g), 1e-2 * np.abs(g).max())))
+        out["oracle"] = "cubic_128 seed 0, oracle PCG to 1e-11"
+    except OSError:
+        out["chom_entry_err_vs_oracle"] = None
+    return out
+
+
+def bench_serve_short(args, n_requests=128):
+    """A short serving pass on the serving workload's mix (Poisson stream of
+    --serve with fewer requests): burst throughput X, then Poisson arrivals at
+    0.7 X; p50/p99 latency (submit -> result) overall and at 64^3."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    reqs = inputs.serving_stream(seed=0, n_requests=n_requests, rate_hz=1.0)
+    opts = lambda warm: shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=args.tol, warm_start=int(warm))
+
+    def replay(ctx, scale):
+        t0 = time.perf_counter()
+        tickets = []
+        for q in reqs:
+            if scale is not None:
+                wait = q.t_arrive * scale - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+            tickets.append((q, shl.shl_serve_submit(ctx.handle, q.design, q.r, opts(q.follow_up_of >= 0),
+                                                    session=q.session)))
+        out = [(q, shl.shl_serve_wait(ctx.handle, t)) for q, t in tickets]
+        return time.perf_counter() - t0, out
+
+    with shl.Context(0, max_batch=args.slots) as ctx:
+        for r in (32, 64, 96):
+            shl.shl_serve_wait(ctx.handle, shl.shl_serve_submit(ctx.handle, reqs[0].design, r, opts(False)))
+        torch.cuda.synchronize()
+        wall1, res1 = replay(ctx, None)
+        X = len(reqs) / wall1
+        span = reqs[-1].t_arrive if reqs[-1].t_arrive > 0 else 1.0
+        wall2, res2 = replay(ctx, (len(reqs) / (0.7 * X)) / span)
+
+    def lat(res, r=None):
+        v = [x["t_done"] - x["t_submit"] for q, x in res if r is None or q.r == r]
+        return (float(np.percentile(v, 50)), float(np.percentile(v, 99))) if v else (None, None)
+    p50, p99 = lat(res2)
+    p50_64, p99_64 = lat(res2, 64)
+    return {"requests": len(reqs), "slots": args.slots, "burst_designs_per_s": X,
+            "poisson_designs_per_s": len(reqs) / wall2, "latency_s": {"p50": p50, "p99": p99, "p50_64": p50_64,
+                                                                      "p99_64": p99_64},
+            "all_converged": all(x["stats"]["status"] == 0 for _, x in res1 + res2),
+            "mix": "32/64/96^3 @ .50/.35/.15, 8-64 charges, 3-20 % solid, 25 % warm-start follow-ups"}
+
+
 def run_serve(args):
     """Serving workload: a Poisson request stream (grids 32^3/64^3/96^3 at
     0.50/0.35/0.15, 8-64 charges, 3-20 % solid, 25 % warm-start follow-ups).
@@ -491,6 +586,7 @@ def main():
     ap.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 128^3 and serving sub-records")
     ap.add_argument("--tol", type=float, default=1e-7,
                     help="relative residual of the cell problems (the metric asks C^H within 1e-4; 1e-7 gives <= 4e-7)")
     ap.add_argument("--serve", action="store_true", help="serving workload (Poisson stream) instead of the bench")
@@ -644,12 +740,35 @@ def main():
         torch.cuda.synchronize()
         s64 = e0.elapsed_time(e1) / 1e3
         compare = {"fp64_designs_per_s": B / s64, "fp64_iters_max": max(max(s["iters"]) for s in st64),
-                   "tol": args.tol, "designs": B}
+                   "fp64_precond": "jacobi", "tol": args.tol, "designs": B}
+        if B == 1:
+            # precision alone: FP32 + refinement with the FP64 mode's point-Jacobi
+            # preconditioner, same design, same tolerance
+            oj = shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=args.tol,
+                                        precond=shl.SHL_PRECOND_JACOBI)
+            e0.record(stream)
+            C32j, st32j = shl.shl_homogenize(h, first[0], r, oj, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s32j = e0.elapsed_time(e1) / 1e3
+            compare.update({"fp32r_jacobi_designs_per_s": 1.0 / s32j, "fp32r_jacobi_iters_max": max(st32j["iters"]),
+                            "same_precond_ratio": s64 / s32j,
+                            "fp32r_mg_designs_per_s": value, "note": "same_precond_ratio = FP32 + refinement over "
+                            "FP64, both point-Jacobi PCG, same design and tolerance"})
+
+    # the rest of the metric: designs/s at 128^3 (O_h designs, C^H against the
+    # oracle's 128^3 value and cubic symmetry) and served p50/p99 latency
+    sub128 = None
+    serve = None
+    if rank == 0 and world == 1 and args.workload == "gaussian64" and not args.no_extra:
+        sub128 = bench_cubic128(h, stream, flush, opts)
+        serve = bench_serve_short(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, per, sample, cores = oracle_sample(designs[0], r, golden_iters(args.workload))
-        cpu = {"value": v, "unit": "designs/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "designs/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "extrapolated": True, "validation": oracle_validate()}
 
     if rank == 0:
         d0 = designs[args.warmup]
@@ -666,7 +785,7 @@ def main():
             "gpu_launches": int(c1 - c0),
             "solver": {"iters_max": [max(s["iters"]) for s in stats], "n_refine": [s["n_refine"] for s in stats],
                        "relres_max": max(max(s["relres"]) for s in stats)},
-            "accuracy": accuracy, "compare": compare,
+            "accuracy": accuracy, "compare": compare, "cubic128": sub128, "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
