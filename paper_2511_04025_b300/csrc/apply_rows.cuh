@@ -87,15 +87,7 @@ inline double build_row_consts(const ElemOp<double> &op, RowConsts *rc) {
 __device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 p2sub(float2 a, float2 b) {
-    unsigned long long ra, rb, rd;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    float2 d;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
-    return d;
-}
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 p2splat(float v) { return make_float2(v, v); }
 
 // ---------------------------------------------------------------------------
@@ -141,21 +133,56 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 // ---------------------------------------------------------------------------
 // Shape of one CTA
 // ---------------------------------------------------------------------------
+// Output node rows per CTA (TY) and resident CTAs per SM the registers are
+// budgeted for (MINB), per grid size.  A CTA's warps spread over the SM's four
+// schedulers, whose register files bound the registers per thread.
+#ifndef SHL_ROWS_TY32
+#define SHL_ROWS_TY32 8
+#endif
+#ifndef SHL_ROWS_MINB32
+#define SHL_ROWS_MINB32 1
+#endif
+#ifndef SHL_ROWS_TY64
+#define SHL_ROWS_TY64 8
+#endif
+#ifndef SHL_ROWS_MINB64
+#define SHL_ROWS_MINB64 1
+#endif
+#ifndef SHL_ROWS_TY128
+#define SHL_ROWS_TY128 4
+#endif
+#ifndef SHL_ROWS_MINB128
+#define SHL_ROWS_MINB128 1
+#endif
+#ifndef SHL_ROWS_TY256
+#define SHL_ROWS_TY256 2
+#endif
+#ifndef SHL_ROWS_MINB256
+#define SHL_ROWS_MINB256 1
+#endif
+#ifndef SHL_ROWS_PD
+#define SHL_ROWS_PD 3
+#endif
+__host__ __device__ constexpr int rows_ty_of(int r) {
+    return r == 32 ? SHL_ROWS_TY32 : (r == 64 ? SHL_ROWS_TY64 : (r == 128 ? SHL_ROWS_TY128 : SHL_ROWS_TY256));
+}
+__host__ __device__ constexpr int rows_minb_of(int r) {
+    return r == 32 ? SHL_ROWS_MINB32 : (r == 64 ? SHL_ROWS_MINB64 : (r == 128 ? SHL_ROWS_MINB128 : SHL_ROWS_MINB256));
+}
+
 template <int R>
 struct RowShape {
     static_assert(R == 32 || R == 64 || R == 128 || R == 256, "row apply: r must be 32, 64, 128 or 256");
-    // output node rows per CTA: the warps of a CTA spread over the SM's four
-    // schedulers, whose register files bound the registers per thread; these
-    // heights keep every instantiation at <= 3 warps per scheduler (<= 168
-    // registers, no spills)
-    static constexpr int TY = R <= 64 ? 8 : (R == 128 ? 4 : 2);
+    static constexpr int TY = rows_ty_of(R);
+    static_assert(R % TY == 0, "row apply: TY must divide r");
+    static constexpr int MINB = rows_minb_of(R);
     static constexpr int P = R / 2;                // element pairs (threads) per row
     static constexpr int NR = TY + 1;              // element rows, row 0 = halo
     static constexpr int NYR = TY + 2;             // node rows per plane
     static constexpr int LIVE = NR * P;            // threads with an element pair
     static constexpr int THREADS = (LIVE + 31) / 32 * 32;
     static constexpr int S = P > 32 ? P / 32 : 1;  // warps per row
-    static constexpr int PD = 3;                   // planes copied ahead of use
+    static constexpr int PD = SHL_ROWS_PD;         // planes copied ahead of use
     static constexpr int NSLOT = PD + 1;           // ring slots
     static constexpr int NODE_BYTES = 3 * NYR * R * 4;
     template <bool SMOOTH>
@@ -186,7 +213,7 @@ __device__ __forceinline__ float2 pair_modulus(const unsigned char *den_row, int
 }
 
 template <int R, bool SMOOTH>
-__global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
+__global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     apply_rows_kernel(const ApplyArgs<float> a, const RowConsts kc) {
     pdl_enter();
     using Sh = RowShape<R>;
@@ -237,11 +264,6 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
             const unsigned bar = bar0 + 8 * slot;
             const unsigned dst0 = smem0 + slot * SLOT;
             const int zt = wrapi(z0 - 1 + t, R);
-            // The slot's previous plane was last read through the generic proxy
-            // before the previous step's barrier, and every value read was
-            // consumed into registers before that barrier, so no read can still
-            // be pending when the copy overwrites the slot (no proxy fence: it
-            // would also wait for this thread's outstanding global stores).
             if (lane == 0) mbar_expect_tx(bar, (unsigned)Sh::template copy_bytes<SMOOTH>());
             __syncwarp();
             // The NYR node rows y0 - 1 .. y0 + TY of a component are contiguous
@@ -276,9 +298,8 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
             if (!mbar_wait_bounded(bar0 + 8 * slot, (unsigned)((t / NSLOT) & 1))) wait_ok = false;
         };
 
-        // top face of plane t: Walsh-Hadamard over x, y of both elements' faces;
-        // own = p at the pair's own nodes (x, x + 1) of node row i
-        auto face = [&](int t, float2 (&ft)[3][4], float2 (&own)[3]) {
+        // top face of plane t: Walsh-Hadamard over x, y of both elements' faces
+        auto face = [&](int t, float2 (&ft)[3][4]) {
             const float *sb = reinterpret_cast<const float *>(smraw + (t % NSLOT) * SLOT);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -288,7 +309,6 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
                 const float b1 = rb[xn];
                 const float2 t0 = *reinterpret_cast<const float2 *>(rt + x);
                 const float t1 = rt[xn];
-                own[c] = b0;
                 const float2 a10 = make_float2(b0.y, b1), a11 = make_float2(t0.y, t1);
                 const float2 s0 = p2add(b0, a10), d0 = p2sub(b0, a10);
                 const float2 s1 = p2add(t0, a11), d1 = p2sub(t0, a11);
@@ -303,29 +323,26 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
         if (warp == 0)
 #pragma unroll 1
             for (int t = 0; t < PD; ++t) issue(t);
-        float2 ftb[3][4], carry[3][4], own_b[3];
+        float2 ftb[3][4], carry[3][4];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int j = 0; j < 4; ++j) carry[c][j] = make_float2(0.f, 0.f);
         wait_plane(0);
-        face(0, ftb, own_b);
+        face(0, ftb);
 
-        const float2 kA = p2splat(kc.amb), kB = p2splat(kc.b), kP = p2splat(kc.p), kQ = p2splat(kc.q),
-                     kF = p2splat(kc.f), kR = p2splat(kc.rr), kD = p2splat(kc.d);
         const int src_lane = P >= 32 ? ((lane + 31) & 31) : ((lane & ~(P - 1)) | ((lane + P - 1) & (P - 1)));
         const bool patch = (S > 1) && live && (lane == 0);  // the row's left neighbour is in another warp
         const int segm1 = (seg + S - 1) % S;
 
 #pragma unroll 1
         for (int s = 0; s <= tz; ++s) {
-            if (warp == 0) issue(s + PD);
             wait_plane(s + 1);
             // moduli of element plane z0 - 1 + s (density rows of plane s)
             const float2 Ee = pair_modulus<SMOOTH>(smraw + (s % NSLOT) * SLOT + Sh::NODE_BYTES + i * DEN_ROW, x,
                                                    a.E, a.Evoid);
-            float2 ftt[3][4], own_t[3];
-            face(s + 1, ftt, own_t);
+            float2 ftt[3][4];
+            face(s + 1, ftt);
             // transformed element displacements u[c][m] (mode m = x + 2y + 4z bits)
             float2 u[3][8];
 #pragma unroll
@@ -337,8 +354,12 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
             }
             // y = E G u in the closed form (the translation modes u[c][0] and
             // y[c][0] are zero)
-            const float2 eA = p2mul(Ee, kA), eB = p2mul(Ee, kB), eP = p2mul(Ee, kP), eQ = p2mul(Ee, kQ),
-                         eF = p2mul(Ee, kF), eR = p2mul(Ee, kR), eD = p2mul(Ee, kD);
+            // E-scaled constants: scalar products with the parameter-bank values
+            // (no registers held for the constants)
+            const float2 eA = make_float2(Ee.x * kc.amb, Ee.y * kc.amb), eB = make_float2(Ee.x * kc.b, Ee.y * kc.b),
+                         eP = make_float2(Ee.x * kc.p, Ee.y * kc.p), eQ = make_float2(Ee.x * kc.q, Ee.y * kc.q),
+                         eF = make_float2(Ee.x * kc.f, Ee.y * kc.f), eR = make_float2(Ee.x * kc.rr, Ee.y * kc.rr),
+                         eD = make_float2(Ee.x * kc.d, Ee.y * kc.d);
             float2 y[3][8];
             {  // c = 0: (u01, u12, u24) -> (y01, y12, y24)
                 const float2 t0 = p2mul(eB, p2add(p2add(u[0][1], u[1][2]), u[2][4]));
@@ -415,6 +436,12 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
                 }
             }
             __syncthreads();
+            // Refill the slot of plane s - 1: every read of it (its face at step
+            // s - 2, its density rows and own-node values at step s - 1) came
+            // before this barrier.  Its values were consumed into registers, so
+            // no proxy fence is needed (one would also wait for this thread's
+            // outstanding global stores).
+            if (warp == 0) issue(s + PD);
             const int ez = z0 - 1 + s;
             if (s >= 1 && live && i >= 1) {
                 const float *ytp = ytop + ((size_t)(par * NR + i - 1) * 3) * R;
@@ -422,6 +449,10 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
                 const float *spt = spill + ((size_t)((par * NR + i - 1) * S + segm1) * 2) * 3;  // row below, left warp
                 const int ny = y0 - 1 + i;  // node row (inside the tile: 0 <= ny - y0 < TY)
                 const size_t nrow = ((size_t)ez * R + ny) * R + x;
+                float *qrow = a.q + (size_t)(3 * k) * N + nrow;
+                const bool pin_here = a.pin && nrow == 0;
+                // p at the pair's own nodes (x, x + 1) of node row i, bottom plane s (for p.q)
+                const float *own = reinterpret_cast<const float *>(smraw + (s % NSLOT) * SLOT) + i * R + x;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float2 otp = *reinterpret_cast<const float2 *>(ytp + c * R + x);
@@ -431,10 +462,11 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
                         otp.x += spt[3 + c];
                     }
                     float2 qv = p2add(p2add(W[c][0], make_float2(recv1, W[c][1].x)), otp);
-                    if (a.pin && nrow == 0) qv.x = 0.f;
-                    *reinterpret_cast<float2 *>(a.q + (size_t)(3 * k + c) * N + nrow) = qv;
+                    if (pin_here) qv.x = 0.f;
+                    *reinterpret_cast<float2 *>(qrow + (size_t)c * N) = qv;
                     if (a.dot) {  // packed compensated sum
-                        const float2 v = a.dot == 1 ? p2mul(qv, own_b[c]) : p2mul(qv, qv);
+                        const float2 v =
+                            a.dot == 1 ? p2mul(qv, *reinterpret_cast<const float2 *>(own + c * NYR * R)) : p2mul(qv, qv);
                         const float2 yv = p2sub(v, dc);
                         const float2 tv = p2add(ds, yv);
                         dc = p2sub(p2sub(tv, ds), yv);
@@ -443,11 +475,9 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, 1)
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                own_b[c] = own_t[c];
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) ftb[c][j] = ftt[c][j];
-            }
         }
         if (!wait_ok && a.err) atomicOr(a.err, kApplyErrWaitTimeout);
         // every plane issued was waited for in the loop; nothing is in flight

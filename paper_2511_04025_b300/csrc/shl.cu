@@ -111,7 +111,7 @@ inline int apply_zc(int r, int nvec) {
 // Row apply (apply_rows.cuh): FP32, r = 32, 64, 128, 256
 // ---------------------------------------------------------------------------
 inline bool rows_grid(int r) { return r == 32 || r == 64 || r == 128 || r == 256; }
-inline int rows_ty(int r) { return r <= 64 ? 8 : (r == 128 ? 4 : 2); }
+inline int rows_ty(int r) { return rows_ty_of(r); }
 
 // Shared-memory opt-in and resident CTAs per SM of one row-apply kernel on
 // the current device (queried once per device).
