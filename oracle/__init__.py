@@ -70,6 +70,8 @@ def lib():
         L.shlo_rhs.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
         L.shlo_solve.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, _dp, _ip, _dp]
+        L.shlo_solve_ex.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_long, ctypes.c_double, ctypes.c_int, _dp, _ip, _dp]
         L.shlo_chom.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 _dp, _dp, _dp]
         L.shlo_element_sensitivity.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -239,6 +241,61 @@ def solve(r: int, rho: np.ndarray, E=1.0, nu=0.3, Evoid=1e-6, tol=1e-12, maxit=2
     st = lib().shlo_solve(r, _p(_rho(rho, r)), E, nu, Evoid, tol, maxit, _p(u),
                           iters.ctypes.data_as(_ip), _p(relres))
     return u, iters, relres, st
+
+
+# --------------------------------------------------------------------------- #
+# Active set (Sec. 4.2.1): culled void, no ersatz floor
+# --------------------------------------------------------------------------- #
+
+CULL_THRESHOLD = 1e-3  # an element is active when beta_e (or the mask) exceeds it
+
+
+def cull(rho: np.ndarray, theta: float = CULL_THRESHOLD) -> np.ndarray:
+    """Element densities of the active set: rho_e where rho_e > theta, else 0
+    (a culled element contributes no stiffness)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.where(rho > theta, rho, 0.0)
+
+
+def active_nodes(r: int, rho_culled: np.ndarray) -> np.ndarray:
+    """Nodes with at least one active incident element (the DOFs the culled
+    problem keeps)."""
+    act = (np.asarray(rho_culled).reshape(r, r, r) > 0.0)  # [iz, iy, ix]
+    out = np.zeros_like(act)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                out |= np.roll(act, shift=(dz, dy, dx), axis=(0, 1, 2))
+    return out.ravel()
+
+
+def solve_active(r: int, rho: np.ndarray, E=1.0, nu=0.3, theta=CULL_THRESHOLD, tol=1e-12, maxit=200000):
+    """The cell problems on the active set of Sec. 4.2.1: elements with
+    rho_e <= theta are culled (zero stiffness, no ersatz floor), active ones
+    have E_e = rho_e E; nodes without an active element are removed (u = 0
+    there) and the first active node is pinned.  Jacobi-PCG in FP64.
+    Returns (u, iters, relres, status, rho_culled, pin)."""
+    rc = cull(_rho(rho, r), theta)
+    nodes = np.flatnonzero(active_nodes(r, rc))
+    if nodes.size == 0:
+        raise ValueError("no active element")
+    pin = int(nodes[0])
+    u = np.empty((6, r ** 3, 3))
+    iters = np.zeros(6, dtype=np.int32)
+    relres = np.zeros(6)
+    st = lib().shlo_solve_ex(r, _p(np.ascontiguousarray(rc)), E, nu, 0.0, pin, tol, maxit, _p(u),
+                             iters.ctypes.data_as(_ip), _p(relres))
+    return u, iters, relres, st, rc, pin
+
+
+def homogenize_active(design, r: int, t: Optional[float] = None, E=1.0, nu=0.3, theta=CULL_THRESHOLD, tol=1e-12,
+                      maxit=200000):
+    """Field -> mask -> C^H on the active set (the solid voxels; no ersatz void)."""
+    vox = voxelize(design, r, t)
+    u, iters, relres, st, rc, pin = solve_active(r, vox["mask"].astype(np.float64), E, nu, theta, tol, maxit)
+    C, Calt = chom(r, rc, u, E, nu, 0.0)
+    vox.update(C=C, Calt=Calt, u=u, iters=iters, relres=relres, status=st, rho=rc, pin=pin)
+    return vox
 
 
 def chom(r: int, rho: np.ndarray, u: np.ndarray, E=1.0, nu=0.3, Evoid=1e-6):

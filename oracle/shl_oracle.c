@@ -421,40 +421,56 @@ int shlo_rhs(int r, const double *rho, double E, double nu, double Evoid, double
 }
 
 /*
- * Solve K u^(k) = f^(k), k = 1..6, with node 0 pinned (its three DOFs
+ * Solve K u^(k) = f^(k), k = 1..6, with node pin_node pinned (its three DOFs
  * removed: zero rows/columns, unit diagonal, zero load), by Jacobi-
- * preconditioned CG in FP64.  All six load cases share each SpMV; each has
- * its own CG scalars and stops once ||f - K u||_2 / ||f||_2 <= tol (the
- * recurrence residual).  relres returns the true residual of the pinned
- * system after the solve; iters the iterations each case used.
- * Returns 0, or 3 if some case hit maxit.
+ * preconditioned CG in FP64.  A node whose diagonal block is zero (every
+ * incident element has zero stiffness: outside the active set of Sec. 4.2.1)
+ * is removed the same way, so its displacement stays 0.  All six load cases
+ * share each SpMV; each has its own CG scalars and stops once
+ * ||f - K u||_2 / ||f||_2 <= tol (the recurrence residual).  relres returns
+ * the true residual of the pinned system after the solve; iters the
+ * iterations each case used.  Returns 0, or 3 if some case hit maxit.
  */
-int shlo_solve(int r, const double *rho, double E, double nu, double Evoid, double tol, int maxit, double *u,
-               int *iters, double *relres) {
+int shlo_solve_ex(int r, const double *rho, double E, double nu, double Evoid, long pin_node, double tol, int maxit,
+                  double *u, int *iters, double *relres) {
     if (r < 1 || !(tol > 0.0) || maxit < 0) return 1;
     const long N = (long)r * r * r;
     const long L = 3 * N;
+    if (pin_node < 0 || pin_node >= N) return 1;
     shlo_bsr A;
     int st = shlo_assemble(r, rho, E, nu, Evoid, &A);
     if (st) return st;
     double *f = (double *)malloc(sizeof(double) * 6 * L);
     shlo_rhs(r, rho, E, nu, Evoid, f);
 
+    /* removed nodes: the pin and every node with a zero diagonal block */
+    char *gone = (char *)calloc((size_t)N, 1);
+    gone[pin_node] = 1;
+    for (long n = 0; n < N; ++n)
+        for (long b = A.rowptr[n]; b < A.rowptr[n + 1]; ++b)
+            if (A.col[b] == n) {
+                int zero = 1;
+                for (int i = 0; i < 9; ++i) zero &= (A.val[9 * b + i] == 0.0);
+                if (zero) gone[n] = 1;
+            }
     /* pinned copy of the operator */
     shlo_bsr P = A;
     P.val = (double *)malloc(sizeof(double) * 9 * A.rowptr[N]);
     memcpy(P.val, A.val, sizeof(double) * 9 * A.rowptr[N]);
     for (long n = 0; n < N; ++n)
         for (long b = P.rowptr[n]; b < P.rowptr[n + 1]; ++b) {
-            if (n == 0 || P.col[b] == 0) {
+            if (gone[n] || gone[P.col[b]]) {
                 for (int i = 0; i < 9; ++i) P.val[9 * b + i] = 0.0;
-                if (n == 0 && P.col[b] == 0) P.val[9 * b] = P.val[9 * b + 4] = P.val[9 * b + 8] = 1.0;
+                if (P.col[b] == n) P.val[9 * b] = P.val[9 * b + 4] = P.val[9 * b + 8] = 1.0;
             }
         }
     double *fp = (double *)malloc(sizeof(double) * 6 * L);
     memcpy(fp, f, sizeof(double) * 6 * L);
     for (int k = 0; k < 6; ++k)
-        for (int i = 0; i < 3; ++i) fp[k * L + i] = 0.0;
+        for (long n = 0; n < N; ++n)
+            if (gone[n])
+                for (int i = 0; i < 3; ++i) fp[k * L + 3 * n + i] = 0.0;
+    free(gone);
 
     /* Jacobi preconditioner: inverse diagonal of the pinned operator */
     double *dinv = (double *)malloc(sizeof(double) * L);
@@ -520,6 +536,12 @@ int shlo_solve(int r, const double *rho, double E, double nu, double Evoid, doub
     free(P.val);
     shlo_free(&A);
     return all ? 0 : 3;
+}
+
+/* The ersatz-void problem: node 0 pinned. */
+int shlo_solve(int r, const double *rho, double E, double nu, double Evoid, double tol, int maxit, double *u,
+               int *iters, double *relres) {
+    return shlo_solve_ex(r, rho, E, nu, Evoid, 0, tol, maxit, u, iters, relres);
 }
 
 /*
