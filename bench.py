@@ -466,6 +466,43 @@ def bench_cubic128(h, stream, flush, opts, n=3):
     return out
 
 
+def bench_active(h, stream, flush, opts, n=10):
+    """The active-set solve (Sec. 4.2.1: void culled, no ersatz floor) on 64^3
+    throughput designs, one at a time, CUDA events on the launch stream, L2
+    flushed between designs; seed 0's C^H against the oracle's active-set
+    value and, as the model gap, against the oracle's ersatz-void value."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    r = 64
+    o = shl.default_solve_opts(precision=opts.precision, tol=opts.tol, active=1)
+    designs = [inputs.gaussian_64(s) for s in range(n + 1)]
+    shl.shl_homogenize(h, designs[n], r, o, stream=stream)  # warm-up
+    ms, its, Cs = [], [], []
+    for d in designs[:n]:
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C, st = shl.shl_homogenize(h, d, r, o, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(max(st["iters"]))
+        Cs.append(C)
+
+    def err(C, name):
+        try:
+            with open(os.path.join(ROOT, "tests", "golden", name + ".json")) as f:
+                g = np.array(json.load(f)["C"])
+        except OSError:
+            return None
+        return float(np.max(np.abs(C - g) / np.maximum(np.abs(g), 1e-2 * np.abs(g).max())))
+    return {"designs_per_s": n / (sum(ms) / 1e3), "ms_per_design": float(np.mean(ms)), "designs": n,
+            "iters_max": its, "tol": opts.tol,
+            "chom_entry_err_vs_oracle_active": err(Cs[0], "gaussian64_s0_active"),
+            "model_gap_vs_ersatz_oracle": err(Cs[0], "gaussian64_s0")}
+
+
 def bench_serve_short(args, n_requests=128):
     """A short serving pass on the serving workload's mix (Poisson stream of
     --serve with fewer requests): burst throughput X, then Poisson arrivals at
@@ -760,8 +797,10 @@ def main():
     # oracle's 128^3 value and cubic symmetry) and served p50/p99 latency
     sub128 = None
     serve = None
+    active = None
     if rank == 0 and world == 1 and args.workload == "gaussian64" and not args.no_extra:
         sub128 = bench_cubic128(h, stream, flush, opts)
+        active = bench_active(h, stream, flush, opts)
         serve = bench_serve_short(args)
 
     cpu = None
@@ -785,7 +824,7 @@ def main():
             "gpu_launches": int(c1 - c0),
             "solver": {"iters_max": [max(s["iters"]) for s in stats], "n_refine": [s["n_refine"] for s in stats],
                        "relres_max": max(max(s["relres"]) for s in stats)},
-            "accuracy": accuracy, "compare": compare, "cubic128": sub128, "serve": serve,
+            "accuracy": accuracy, "compare": compare, "cubic128": sub128, "active_set": active, "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

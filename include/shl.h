@@ -129,6 +129,16 @@ typedef struct {
  *                  lambda_max estimated by power iteration at setup (<= 0: 1.6);
  *                  if the preconditioned CG still breaks down, the solve is
  *                  repeated with point Jacobi
+ *   active         0 (default): every element carries stiffness, void ones the
+ *                  ersatz E_void.  1: the active set of Sec. 4.2.1 -- elements
+ *                  with rho_e <= cull are culled (no stiffness, no ersatz
+ *                  floor), active ones have E_e = rho_e E, nodes with no active
+ *                  element drop out of the solve (u = 0 there) and C^H sums the
+ *                  active elements.  The result is the E_void -> 0 limit of the
+ *                  ersatz problem (first order in E_void).  Floating pieces of
+ *                  solid make the system singular but consistent; CG converges
+ *                  on it.  Not available in shl_grad (SHL_EINVAL).
+ *   cull           density threshold of the active set (<= 0 selects 1e-3)
  */
 typedef struct {
     double E, nu, E_void;
@@ -142,6 +152,8 @@ typedef struct {
     int32_t precond;
     int32_t mg_nu;
     double mg_omega;
+    int32_t active;
+    double cull;
 } shl_solve_opts;
 
 /* Per-result record. */

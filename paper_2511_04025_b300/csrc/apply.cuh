@@ -434,8 +434,14 @@ __global__ void dinv_kernel(int r, const uint8_t *mask, const double *rho, doubl
                              wrapi(ix - (b & 1), r);
             s += elem_modulus(mask, rho, e, E, Ev);
         }
-        dinv[n] = (T)(1.0 / (kdiag * s));
+        dinv[n] = s > 0.0 ? (T)(1.0 / (kdiag * s)) : T(0);  // no active element: the node drops out
     }
+}
+
+// Densities of the active set (Sec. 4.2.1): rho_e where rho_e > theta, else 0.
+__global__ void cull_rho_kernel(size_t N, const double *rho, double theta, double *out) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = rho[e] > theta ? rho[e] : 0.0;
 }
 
 // f^(k)_n = - sum over the 8 incident elements of E_e (Khat chi^k)_(corner of n)

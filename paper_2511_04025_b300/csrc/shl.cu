@@ -384,7 +384,7 @@ inline int run_select(shl_ctx *ctx, const double *dd, size_t n, double vf, cudaS
     const int widths[6] = {11, 11, 11, 11, 11, 9};
     for (int p = 0; p < 6; ++p) {
         select_hist_kernel<<<g, 256, 0, s>>>(keys, n, st, shifts[p], widths[p]);
-        select_choose_kernel<<<1, 256, 0, s>>>(st, shifts[p]);
+        select_choose_kernel<<<1, kSelChooseThreads, 0, s>>>(st, shifts[p]);
         ctx->launches += 2;
     }
     select_gather_kernel<<<g, 256, 0, s>>>(keys, n, st);
@@ -1406,6 +1406,8 @@ inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
         return set_err(ctx, SHL_EINVAL, "unknown preconditioner %d", o->precond);
     if (!(o->mg_omega <= 0.0 || o->mg_omega < 2.0))
         return set_err(ctx, SHL_EINVAL, "mg_omega (damping times lambda_max) must be < 2");
+    if (o->active != 0 && o->active != 1) return set_err(ctx, SHL_EINVAL, "active must be 0 or 1, got %d", o->active);
+    if (o->active && !(o->cull < 1.0)) return set_err(ctx, SHL_EINVAL, "cull threshold %g must be < 1", o->cull);
     return SHL_OK;
 }
 
@@ -1418,6 +1420,20 @@ inline int solve_impl(shl_ctx *ctx, int r, const uint8_t *mask_dev, const double
     double *x64 = u_dev;
     if (!x64) SHL_TRY(ws_get_t(ctx, "x64", NV, &x64));
     Density den{mask_dev, rho_dev, o->E, o->E_void};
+    if (o->active) {
+        // active set (Sec. 4.2.1): no ersatz floor, culled elements carry no
+        // stiffness (a mask is its own active set); nodes left with a zero
+        // diagonal get zero (block) inverses and so never change
+        den.Ev = 0.0;
+        if (rho_dev) {
+            const size_t N = (size_t)r * r * r;
+            double *rc = nullptr;
+            SHL_TRY(ws_get_t(ctx, "rho_active", N, &rc));
+            cull_rho_kernel<<<grid1d(N), kBlk, 0, s>>>(N, rho_dev, o->cull > 0.0 ? o->cull : 1e-3, rc);
+            ++ctx->launches;
+            den.rho = rc;
+        }
+    }
     SolveOut so;
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0);
@@ -1638,6 +1654,8 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->precond = SHL_PRECOND_MG;
     o->mg_nu = 1;
     o->mg_omega = 1.6;
+    o->active = 0;
+    o->cull = 1e-3;
 }
 
 int shl_create(const shl_opts *opts, shl_ctx **out) {
@@ -1802,6 +1820,8 @@ int shl_grad(shl_ctx *ctx, const shl_design *d, int32_t r, const shl_solve_opts 
     SHL_TRY(validate_design(ctx, d, r));
     if (o->density != SHL_SMOOTH)
         return set_err(ctx, SHL_EINVAL, "shl_grad needs the smooth density (the binary mask has no derivative)");
+    if (o->active)
+        return set_err(ctx, SHL_EINVAL, "shl_grad differentiates the ersatz-void problem; active = 1 is forward only");
     if (!dE_dC) return set_err(ctx, SHL_EINVAL, "dE_dC is NULL");
     for (int i = 0; i < 36; ++i)
         if (!std::isfinite(dE_dC[i])) return set_err(ctx, SHL_EINVAL, "non-finite dE_dC");

@@ -49,6 +49,31 @@ def make(name: str):
     print(name, f"{dt:.1f}s", out["iters"], out["relres"], flush=True)
 
 
+# The active-set problem (Sec. 4.2.1: void culled, no ersatz floor) on the
+# same designs.
+ACTIVE_CASES = {
+    "plain32_s0_active": (lambda: inputs.plain_32(0), 32, 1e-12),
+    "gaussian64_s0_active": (lambda: inputs.gaussian_64(0), 64, 1e-12),
+}
+
+
+def make_active(name: str):
+    mk, r, tol = ACTIVE_CASES[name]
+    d = mk()
+    t0 = time.time()
+    res = oracle.homogenize_active(d, r, tol=tol)
+    dt = time.time() - t0
+    out = dict(
+        name=name, r=r, t=res["t"], n_solid=int(res["mask"].sum()), pin=res["pin"],
+        n_active_nodes=int(oracle.active_nodes(r, res["rho"]).sum()), C=res["C"].tolist(),
+        iters=[int(i) for i in res["iters"]], relres=[float(x) for x in res["relres"]], status=int(res["status"]),
+        oracle_seconds=dt, oracle_threads=oracle.num_threads(), tol=tol,
+        source="oracle.homogenize_active (FP64 CPU), tests/golden/make_golden.py")
+    with open(os.path.join(HERE, f"{name}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, f"{dt:.1f}s", out["iters"], out["relres"], flush=True)
+
+
 # Inverse-design gradient at full size: 64^3, 24 charges +-1, 10 % solid
 # (t from the binary rule, then held fixed), smoothed density with
 # kappa = ln(9) r, objective sum (C^H - C^T)^2 with C^T isotropic (bulk 0.05,
@@ -84,5 +109,10 @@ def make_grad(name: str):
 
 
 if __name__ == "__main__":
-    for n in (sys.argv[1:] or list(CASES) + list(GRAD_CASES)):
-        make_grad(n) if n in GRAD_CASES else make(n)
+    for n in (sys.argv[1:] or list(CASES) + list(GRAD_CASES) + list(ACTIVE_CASES)):
+        if n in GRAD_CASES:
+            make_grad(n)
+        elif n in ACTIVE_CASES:
+            make_active(n)
+        else:
+            make(n)
