@@ -217,26 +217,70 @@ __global__ void select_hist_kernel(const unsigned long long *__restrict__ keys, 
     }
 }
 
-__global__ void select_choose_kernel(SelectState *st, int shift) {
-    if (threadIdx.x < 2) {
-        const int w = threadIdx.x;
-        const unsigned long long rank = st->rank[w];
-        unsigned long long acc = 0;
-        int bin = kSelBins - 1;
-        for (int b = 0; b < kSelBins; ++b) {
-            const unsigned c = st->hist[w][b];
-            if (acc + c >= rank) {
-                bin = b;
-                break;
-            }
-            acc += c;
+// Choose the digit whose bin holds the wanted rank, for both ranks at once.
+// One block of kSelChooseThreads threads: thread t owns bins
+// [t * PER, (t + 1) * PER); a block-wide exclusive prefix sum of the per-thread
+// counts finds the one thread whose range the rank falls in, which then walks
+// its PER bins.  Same result as scanning the bins in order (bin = first b
+// with count(<= b) >= rank; the last bin and the full total when none is).
+constexpr int kSelChooseThreads = 256;
+__global__ void __launch_bounds__(kSelChooseThreads) select_choose_kernel(SelectState *st, int shift) {
+    constexpr int T = kSelChooseThreads, PER = kSelBins / T, NW = T / 32;
+    static_assert(kSelBins % T == 0, "bins per thread");
+    __shared__ unsigned long long wsum[2][NW];
+    __shared__ unsigned long long total[2];
+    __shared__ int hit[2];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned c[2][PER];
+    unsigned long long own[2], incl[2];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+        own[w] = 0;
+#pragma unroll
+        for (int b = 0; b < PER; ++b) {
+            c[w][b] = st->hist[w][t * PER + b];
+            own[w] += c[w][b];
         }
-        st->rank[w] = rank - acc;
-        st->prefix[w] |= ((unsigned long long)bin) << shift;
-        if (shift == 0) st->key[w] = st->prefix[w];
+        incl[w] = own[w];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl[w], o);
+            if (lane >= o) incl[w] += v;
+        }
+        if (lane == 31) wsum[w][warp] = incl[w];
+    }
+    if (t < 2) hit[t] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+        unsigned long long before = incl[w] - own[w];  // exclusive prefix within the warp
+        for (int k = 0; k < warp; ++k) before += wsum[w][k];
+        if (t == T - 1) total[w] = before + own[w];
+        const unsigned long long rank = st->rank[w];
+        if ((before < rank || t == 0) && rank <= before + own[w]) {  // the rank falls in this thread's bins
+            unsigned long long acc = before;
+            int bin = t * PER + PER - 1;
+#pragma unroll
+            for (int b = 0; b < PER; ++b)
+                if (acc + c[w][b] >= rank) {
+                    bin = t * PER + b;
+                    break;
+                } else {
+                    acc += c[w][b];
+                }
+            hit[w] = 1;
+            st->rank[w] = rank - acc;
+            st->prefix[w] |= ((unsigned long long)bin) << shift;
+            if (shift == 0) st->key[w] = st->prefix[w];
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * kSelBins; i += blockDim.x) (&st->hist[0][0])[i] = 0;
+    if (t < 2 && !hit[t]) {  // the rank exceeds the total: the last bin
+        st->rank[t] = st->rank[t] - total[t];
+        st->prefix[t] |= ((unsigned long long)(kSelBins - 1)) << shift;
+        if (shift == 0) st->key[t] = st->prefix[t];
+    }
+    for (int i = t; i < 2 * kSelBins; i += T) (&st->hist[0][0])[i] = 0;
 }
 
 __global__ void select_gather_kernel(const unsigned long long *__restrict__ keys, size_t n, SelectState *st) {
