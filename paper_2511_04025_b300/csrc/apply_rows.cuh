@@ -163,6 +163,9 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 #ifndef SHL_ROWS_PD
 #define SHL_ROWS_PD 3
 #endif
+#ifndef SHL_ROWS_ZUNROLL
+#define SHL_ROWS_ZUNROLL 2
+#endif
 __host__ __device__ constexpr int rows_ty_of(int r) {
     return r == 32 ? SHL_ROWS_TY32 : (r == 64 ? SHL_ROWS_TY64 : (r == 128 ? SHL_ROWS_TY128 : SHL_ROWS_TY256));
 }
@@ -335,7 +338,10 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
         const bool patch = (S > 1) && live && (lane == 0);  // the row's left neighbour is in another warp
         const int segm1 = (seg + S - 1) % S;
 
-#pragma unroll 1
+        // unrolled by two: the face arrays alternate roles between the copies
+        // instead of being copied every plane
+        constexpr int ZU = SHL_ROWS_ZUNROLL;
+#pragma unroll ZU
         for (int s = 0; s <= tz; ++s) {
             wait_plane(s + 1);
             // moduli of element plane z0 - 1 + s (density rows of plane s)
