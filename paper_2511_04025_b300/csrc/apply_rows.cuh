@@ -135,7 +135,11 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 // ---------------------------------------------------------------------------
 // Output node rows per CTA (TY) and resident CTAs per SM the registers are
 // budgeted for (MINB), per grid size.  A CTA's warps spread over the SM's four
-// schedulers, whose register files bound the registers per thread.
+// schedulers, whose register files bound the registers per thread; the
+// per-plane barrier makes the scheduler with the most warps set the pace.
+// Measured on B300 (us per launch): r = 64: TY 8 (9 warps) 22.4, 7 (8 warps)
+// 26.2, 15 (16 warps) 22.8; r = 128: TY 3 (8 warps) 174, 4 (10) 163, 7 (16,
+// 124 registers) 138; r = 256: TY 2 (12 warps) 1256, 3 (16) 1110.
 #ifndef SHL_ROWS_TY32
 #define SHL_ROWS_TY32 8
 #endif
@@ -149,13 +153,13 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 #define SHL_ROWS_MINB64 1
 #endif
 #ifndef SHL_ROWS_TY128
-#define SHL_ROWS_TY128 4
+#define SHL_ROWS_TY128 7
 #endif
 #ifndef SHL_ROWS_MINB128
 #define SHL_ROWS_MINB128 1
 #endif
 #ifndef SHL_ROWS_TY256
-#define SHL_ROWS_TY256 2
+#define SHL_ROWS_TY256 3
 #endif
 #ifndef SHL_ROWS_MINB256
 #define SHL_ROWS_MINB256 1
@@ -177,7 +181,9 @@ template <int R>
 struct RowShape {
     static_assert(R == 32 || R == 64 || R == 128 || R == 256, "row apply: r must be 32, 64, 128 or 256");
     static constexpr int TY = rows_ty_of(R);
-    static_assert(R % TY == 0, "row apply: TY must divide r");
+    // TY need not divide r: the last tile's rows past the grid wrap around,
+    // are computed and not stored
+    static_assert(TY >= 1 && TY + 2 <= R, "row apply: 1 <= TY <= r - 2");
     static constexpr int MINB = rows_minb_of(R);
     static constexpr int P = R / 2;                // element pairs (threads) per row
     static constexpr int NR = TY + 1;              // element rows, row 0 = halo
@@ -449,11 +455,11 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
             // outstanding global stores).
             if (warp == 0) issue(s + PD);
             const int ez = z0 - 1 + s;
-            if (s >= 1 && live && i >= 1) {
+            if (s >= 1 && live && i >= 1 && y0 - 1 + i < R) {
                 const float *ytp = ytop + ((size_t)(par * NR + i - 1) * 3) * R;
                 const float *spb = spill + ((size_t)((par * NR + i) * S + segm1) * 2) * 3;      // own row, left warp
                 const float *spt = spill + ((size_t)((par * NR + i - 1) * S + segm1) * 2) * 3;  // row below, left warp
-                const int ny = y0 - 1 + i;  // node row (inside the tile: 0 <= ny - y0 < TY)
+                const int ny = y0 - 1 + i;  // node row (inside the tile and the grid)
                 const size_t nrow = ((size_t)ez * R + ny) * R + x;
                 float *qrow = a.q + (size_t)(3 * k) * N + nrow;
                 const bool pin_here = a.pin && nrow == 0;

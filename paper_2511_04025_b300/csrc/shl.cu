@@ -149,7 +149,7 @@ inline int rows_occupancy(int r, bool smooth) {
 // z chunks of the row apply: the same makespan model as pick_zc over
 // r / TY row tiles per load case.
 inline int pick_zc_rows(int r, int nvec, int ctas_per_sm) {
-    const long long nxy = (long long)(r / rows_ty(r)) * nvec;
+    const long long nxy = (long long)((r + rows_ty(r) - 1) / rows_ty(r)) * nvec;
     const long long slots = 148LL * ctas_per_sm;
     int best = 1;
     long long best_cost = -1;
@@ -176,7 +176,7 @@ inline ApplyGeom apply_geom(int r, int nvec, const uint8_t *mask, const double *
     const void *den = rho ? (const void *)rho : (const void *)mask;
     if (std::is_same<T, float>::value && rows_grid(r) && den && (reinterpret_cast<uintptr_t>(den) & 15) == 0) {
         const int occ = rows_occupancy(r, rho != nullptr);
-        if (occ > 0) return ApplyGeom{r / rows_ty(r), pick_zc_rows(r, nvec, occ), 1};
+        if (occ > 0) return ApplyGeom{(r + rows_ty(r) - 1) / rows_ty(r), pick_zc_rows(r, nvec, occ), 1};
     }
     return ApplyGeom{((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY), apply_zc<T>(r, nvec), 0};
 }
