@@ -284,6 +284,7 @@ def run_field(args):
     rows = []
     with shl.Context(0) as ctx:
         h = ctx.handle
+        fp64_peak = shl.shl_probe_peaks(h)["fp64_fma_gflops"]
         stream = torch.cuda.Stream()
         for r, n in FIELD_SHAPES:
             d = inputs.random_design(7, n, 0.1)
@@ -308,9 +309,10 @@ def run_field(args):
     line = {"metric": "field evaluation time, F and grad F (r=256, 2N=256)", "value": last["ms"], "unit": "ms",
             "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "field (paper Table 1 shapes)", "K": 3},
-            "roofline": {"bound": "fp64", "achieved": last["fp64_gflops"], "peak": FP64_NOMINAL_GFLOPS,
-                         "unit": "GFLOP/s", "frac": last["fp64_gflops"] / FP64_NOMINAL_GFLOPS,
-                         "peak_kind": "nominal", "traffic": None},
+            "roofline": {"bound": "fp64", "achieved": last["fp64_gflops"], "peak": fp64_peak,
+                         "unit": "GFLOP/s", "frac": last["fp64_gflops"] / fp64_peak,
+                         "peak_kind": "measured (shl_probe_peaks: FP64 FMA throughput)", "traffic": None,
+                         "nominal_peak": FP64_NOMINAL_GFLOPS},
             "shapes": rows}
     print(json.dumps(line), flush=True)
 
@@ -511,6 +513,102 @@ def bench_active(h, stream, flush, opts, n=10):
             "iters_max": its, "tol": opts.tol,
             "chom_entry_err_vs_oracle_active": err(Cs[0], "gaussian64_s0_active"),
             "model_gap_vs_ersatz_oracle": err(Cs[0], "gaussian64_s0")}
+
+
+def _golden(name):
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", name + ".json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def _entry_err(C, Cref):
+    Cref = np.asarray(Cref)
+    return float(np.max(np.abs(C - Cref) / np.maximum(np.abs(Cref), 1e-2 * np.abs(Cref).max())))
+
+
+def bench_plain32(h, stream, n=3):
+    """The plain method of the first configuration: 32^3, 8 charges +-1, 15 %
+    solid, FP64 PCG (point Jacobi) to a relative residual of 1e-10; seed 0's
+    C^H against the oracle's (solved to 1e-12)."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    o = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-10)
+    shl.shl_homogenize(h, inputs.plain_32(n), 32, o, stream=stream)  # warm-up
+    ms, Cs, its = [], [], []
+    for sd in range(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C, st = shl.shl_homogenize(h, inputs.plain_32(sd), 32, o, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        Cs.append(C)
+        its.append(max(st["iters"]))
+    g = _golden("plain32_s0")
+    return {"designs_per_s": n / (sum(ms) / 1e3), "ms_per_design": float(np.mean(ms)), "designs": n,
+            "precision": "fp64", "tol": 1e-10, "iters_max": its,
+            "chom_entry_err_vs_oracle": _entry_err(Cs[0], g["C"]) if g else None}
+
+
+def bench_grad64(h, stream, n=8):
+    """Inverse-design gradients at 64^3 (the fifth configuration): n designs,
+    24 charges +-1, 10 % solid, smoothed density, FP32 + refinement at tol
+    1e-10, dE/dC^H = 2 (C^H - C^T); forward and adjoint through shl_grad.
+    Seed 0 with the stored dE/dC^H against the oracle's gradient (every
+    parameter, relative to the largest entry)."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    o = shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10, density=shl.SHL_SMOOTH)
+    Ct = inputs.isotropic_target()
+    g = _golden("gradient64_s0")
+    ts = [shl.shl_voxelize(h, inputs.gradient_64(sd), 64, stream=stream)["t"] for sd in range(n)]
+    u = torch.empty(18 * 64 ** 3, dtype=torch.float64, device="cuda")
+    shl.shl_grad(h, inputs.gradient_64(0), 64, o, np.zeros((6, 6)), u=u, t=ts[0], stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sd in range(n):
+        d = inputs.gradient_64(sd)
+        fwd = shl.shl_grad(h, d, 64, o, np.zeros((6, 6)), u=u, t=ts[sd], stream=stream)
+        ob = shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10, density=shl.SHL_SMOOTH, warm_start=1)
+        shl.shl_grad(h, d, 64, ob, 2.0 * (fwd["C"] - Ct), u=u, t=ts[sd], want_alpha=True, stream=stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    err = None
+    if g:
+        out = shl.shl_grad(h, inputs.gradient_64(0), 64, o, np.array(g["dEdC"]), t=g["t"], want_alpha=True,
+                           stream=stream)
+        scale = max(np.abs(g["g_pos"]).max(), np.abs(g["g_q"]).max(), abs(g["g_iso"]), abs(g["g_t"]),
+                    np.abs(g["g_alpha"]).max())
+        err = max(np.abs(out["g_pos"] - np.array(g["g_pos"])).max(), np.abs(out["g_q"] - np.array(g["g_q"])).max(),
+                  abs(out["g_iso"] - g["g_iso"]), abs(out["g_t"] - g["g_t"]),
+                  np.abs(out["g_alpha"] - np.array(g["g_alpha"])).max()) / scale
+    return {"gradients_per_s": n / wall, "ms_per_gradient": 1e3 * wall / n, "designs": n, "tol": 1e-10,
+            "clock": "host wall clock around forward + adjoint (each returns its results to the host)",
+            "grad_rel_err_vs_oracle": None if err is None else float(err)}
+
+
+def bench_field256(h, stream):
+    """Field evaluation on the largest shape of the paper's field-timing table
+    (r = 256, 2N = 256 charges): F and grad F in FP64, CUDA events."""
+    import torch
+    from paper_2511_04025_b300 import inputs, shl
+    d = inputs.random_design(7, 256, 0.1)
+    F = torch.empty(256 ** 3, dtype=torch.float64, device="cuda")
+    gF = torch.empty(256 ** 3, 3, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        shl.shl_field(h, d, 256, F, gF, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        shl.shl_field(h, d, 256, F, gF, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    del F, gF
+    return {"ms": ms, "r": 256, "charges": 256, "paper_h200_ms": FIELD_PAPER_H200_MS[(256, 256)],
+            "fp64_gflops": 2.0 * 4 * 7 * 256 ** 3 / ms / 1e6}
 
 
 def bench_serve_short(args, n_requests=128):
@@ -748,6 +846,7 @@ def main():
     # the launch stream on the last design's mask
     apply_s = time_apply(h, r, designs[-1], stream)
     roofline = apply_roofline(r, apply_s)
+    arith_peaks = shl.shl_probe_peaks(h)
 
     # accuracy of the timed designs (untimed): C^H against the plain FP64 GPU
     # path solved to 1e-11, entry error relative to max(|C_ij|, 1e-2 max|C|);
@@ -800,12 +899,13 @@ def main():
 
     # the rest of the metric: designs/s at 128^3 (O_h designs, C^H against the
     # oracle's 128^3 value and cubic symmetry) and served p50/p99 latency
-    sub128 = None
-    serve = None
-    active = None
+    sub128 = serve = active = plain32 = grad64 = field256 = None
     if rank == 0 and world == 1 and args.workload == "gaussian64" and not args.no_extra:
         sub128 = bench_cubic128(h, stream, flush, opts)
         active = bench_active(h, stream, flush, opts)
+        plain32 = bench_plain32(h, stream)
+        grad64 = bench_grad64(h, stream)
+        field256 = bench_field256(h, stream)
         serve = bench_serve_short(args)
 
     cpu = None
@@ -825,10 +925,11 @@ def main():
             "config": bench_config(args, r, desc, world),
             "e2e": {"value": e2e, "unit": "designs/s", "h2d_bytes_per_step": int(B * (d0.pos.nbytes + d0.q.nbytes)),
                     "d2h_bytes_per_step": B * 36 * 8},
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "roofline": roofline, "arith_peaks_gflops": arith_peaks, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(c1 - c0),
             "solver": solver_summary(stats),
             "accuracy": accuracy, "compare": compare, "cubic128": sub128, "active_set": active, "serve": serve,
+            "plain32_fp64": plain32, "grad64": grad64, "field256": field256,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -341,6 +341,19 @@ typedef struct {
 } shl_counters;
 int shl_get_counters(shl_ctx *ctx, shl_counters *out);
 
+/* Arithmetic peaks of the context's device, measured by short FMA-throughput
+ * kernels (independent FMA chains in every thread of 4 CTAs per SM): scalar
+ * FP32, packed FP32 pairs and FP64, in GFLOP/s (an FMA counts 2 flop, a packed
+ * FMA 4).  The ceilings beside the copy rate for kernels bound by CUDA-core
+ * arithmetic (the FP64 field evaluation of Sec. 3.1, the FP32 stiffness
+ * apply).  Synchronises the context's stream; takes a few milliseconds. */
+typedef struct {
+    double fp32_fma_gflops;
+    double fp32x2_fma_gflops;
+    double fp64_fma_gflops;
+} shl_peaks;
+int shl_probe_peaks(shl_ctx *ctx, shl_peaks *out);
+
 /*
  * Allocation-free variant of shl_chom (the paper has no counterpart; this is
  * an interface for callers that cannot allocate device memory, e.g. code

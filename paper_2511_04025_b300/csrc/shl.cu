@@ -6,6 +6,7 @@
 #include "element.cuh"
 #include "field.cuh"
 #include "pcg.cuh"
+#include "probe.cuh"
 #include "adjoint.cuh"
 #include "mg.cuh"
 #include "vec.cuh"
@@ -1893,6 +1894,43 @@ int shl_homogenize_batch(shl_ctx *ctx, int32_t n, const shl_design *d, const int
         if (e) cudaEventDestroy(e);
     cudaEventDestroy(entry);
     return err != SHL_OK ? err : worst;
+}
+
+int shl_probe_peaks(shl_ctx *ctx, shl_peaks *out) {
+    if (!ctx || !out) return set_err(ctx, SHL_EINVAL, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    int nsm = 0;
+    SHL_CUDA(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int threads = 512, blocks = nsm * 4;
+    float *buf = nullptr;
+    SHL_TRY(ws_get_t(ctx, "probe_out", (size_t)threads * blocks, &buf));
+    cudaEvent_t e0, e1;
+    SHL_CUDA(ctx, cudaEventCreate(&e0));
+    SHL_CUDA(ctx, cudaEventCreate(&e1));
+    // flop/s = threads x blocks x iters x chains x (2 per FMA, 4 per packed FMA) / seconds
+    auto timed = [&](int kind, int iters, double flops_per_fma) -> double {
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up, the second is timed
+            cudaEventRecord(e0, s);
+            if (kind == 0) probe_ffma_kernel<<<blocks, threads, 0, s>>>(iters, 0.999f, 1e-3f, buf);
+            if (kind == 1) probe_ffma2_kernel<<<blocks, threads, 0, s>>>(iters, 0.999f, 1e-3f, buf);
+            if (kind == 2) probe_dfma_kernel<<<blocks, threads, 0, s>>>(iters, 0.999, 1e-3, buf);
+            cudaEventRecord(e1, s);
+        }
+        ctx->launches += 2;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return (double)threads * blocks * iters * kProbeChains * flops_per_fma / (ms * 1e-3) / 1e9;
+    };
+    out->fp32_fma_gflops = timed(0, 4096, 2.0);
+    out->fp32x2_fma_gflops = timed(1, 4096, 4.0);
+    out->fp64_fma_gflops = timed(2, 256, 2.0);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SHL_CUDA(ctx, cudaGetLastError());
+    return SHL_OK;
 }
 
 int shl_get_counters(shl_ctx *ctx, shl_counters *out) {

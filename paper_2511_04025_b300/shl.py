@@ -101,6 +101,7 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(shl_solve_opts), _dp,
                                             ctypes.POINTER(shl_stats), _vp]),
     "shl_get_counters": (ctypes.c_int, [_vp, ctypes.c_void_p]),
+    "shl_probe_peaks": (ctypes.c_int, [_vp, ctypes.c_void_p]),
     "shl_chom_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _vp, _vp, _vp]),
     "shl_grad": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32, ctypes.POINTER(shl_solve_opts), _dp,
@@ -407,3 +408,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class shl_peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_gflops", ctypes.c_double), ("fp32x2_fma_gflops", ctypes.c_double),
+                ("fp64_fma_gflops", ctypes.c_double)]
+
+
+def shl_probe_peaks(ctx) -> dict:
+    """Measured FP32, packed-FP32 and FP64 FMA throughput of the context's device (GFLOP/s)."""
+    p = shl_peaks()
+    _check(ctx, lib().shl_probe_peaks(ctx, ctypes.byref(p)))
+    return dict(fp32_fma_gflops=p.fp32_fma_gflops, fp32x2_fma_gflops=p.fp32x2_fma_gflops,
+                fp64_fma_gflops=p.fp64_fma_gflops)

@@ -347,3 +347,12 @@ def test_multigrid_survives_void_held_mechanisms_at_128(ctx, seed):
     dev = [C[0, 0] - C[1, 1], C[0, 0] - C[2, 2], C[0, 1] - C[0, 2], C[0, 1] - C[1, 2], C[3, 3] - C[4, 4],
            C[3, 3] - C[5, 5], C[0, 3], C[1, 4], C[2, 5], C[3, 4]]
     assert np.max(np.abs(dev)) <= 1e-6 * s
+
+
+def test_probe_peaks_are_plausible(ctx):
+    """Measured FMA throughput: positive, packed FP32 pairs at least as fast as
+    scalar FP32, FP64 far below FP32 on this part."""
+    p = shl.shl_probe_peaks(ctx)
+    assert p["fp32_fma_gflops"] > 1e3 and p["fp64_fma_gflops"] > 10.0
+    assert p["fp32x2_fma_gflops"] >= 0.9 * p["fp32_fma_gflops"]
+    assert p["fp64_fma_gflops"] < 0.5 * p["fp32_fma_gflops"]
