@@ -178,7 +178,8 @@ def dist_setup(n_gpus):
 def bench_config(args, r, desc, world):
     """The workload the headline line is quoted on (both arms print it)."""
     B = max(1, args.batch_designs)
-    return {"workload": args.workload, "desc": desc, "r": r, "precision": args.precision, "tol": args.tol,
+    return {"workload": args.workload, "desc": desc + (", active set (void culled)" if args.active else ""), "r": r,
+            "precision": args.precision, "tol": args.tol,
             "l2": "flushed between steps", "parallelism": f"replicas x{world}",
             "batch": f"{B} designs per step, concurrent on {min(B, args.slots)} serving slots"}
 
@@ -731,7 +732,9 @@ def main():
     ap.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 128^3 and serving sub-records")
+    ap.add_argument("--no-extra", action="store_true", help="skip the sub-records (128^3, serving, active set, ...)")
+    ap.add_argument("--active", action="store_true",
+                    help="solve the active-set problem (void culled, no ersatz floor) instead of the ersatz one")
     ap.add_argument("--tol", type=float, default=1e-7,
                     help="relative residual of the cell problems (the metric asks C^H within 1e-4; 1e-7 gives <= 4e-7)")
     ap.add_argument("--serve", action="store_true", help="serving workload (Poisson stream) instead of the bench")
@@ -773,7 +776,7 @@ def main():
     torch.cuda.set_device(local)
     gen, r, desc = WORKLOADS[args.workload]
     prec = shl.SHL_FP32_REFINE if args.precision == "fp32r" else shl.SHL_FP64
-    opts = shl.default_solve_opts(precision=prec, tol=args.tol)
+    opts = shl.default_solve_opts(precision=prec, tol=args.tol, active=int(args.active))
     ctx = shl.Context(local, max_batch=args.slots)
     h = ctx.handle
     stream = torch.cuda.Stream()
@@ -851,10 +854,10 @@ def main():
     # accuracy of the timed designs (untimed): C^H against the plain FP64 GPU
     # path solved to 1e-11, entry error relative to max(|C_ij|, 1e-2 max|C|);
     # every design of the first timed batch and the first of each later one
-    ref = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-11)
-    ref_desc = "FP64 GPU path, tol 1e-11"
+    ref = shl.default_solve_opts(precision=shl.SHL_FP64, tol=1e-11, active=int(args.active))
+    ref_desc = "FP64 GPU path, tol 1e-11" + (", same active set" if args.active else "")
     if r >= 256:  # the FP64 mode (point Jacobi) takes minutes per design here
-        ref = shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10)
+        ref = shl.default_solve_opts(precision=shl.SHL_FP32_REFINE, tol=1e-10, active=int(args.active))
         ref_desc = "same path at tol 1e-10 (self-consistency; no FP64 reference at 256^3)"
     acc = 0.0
     check = list(range(min(B, 8))) + [k * B for k in range(1, args.steps)]

@@ -587,6 +587,28 @@ inline void launch_vec_update(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom 
     ++ctx->launches;
 }
 
+// Active set: the vector kernels visit only the chunks holding a node with an
+// active element (listed in ascending order, so every reduction keeps a fixed
+// order).  One host synchronisation (the count), at setup.
+inline int active_chunk_list(shl_ctx *ctx, int r, const Density &den, VecGeom *g, cudaStream_t s) {
+    const size_t nchunks = g->chunks;
+    const int nb = (int)((nchunks + kChunkBlock - 1) / kChunkBlock);
+    unsigned *counts = nullptr, *list = nullptr;
+    SHL_TRY(ws_get_t(ctx, "active_chunk_counts", (size_t)nb + 1, &counts));
+    SHL_TRY(ws_get_t(ctx, "active_chunk_list", nchunks, &list));
+    chunk_count_kernel<<<nb, kVecThreads, 0, s>>>(r, g->V, nchunks, den.mask, den.rho, counts);
+    chunk_scan_kernel<<<1, 1024, 0, s>>>(nb, counts, counts + nb);
+    chunk_write_kernel<<<nb, kVecThreads, 0, s>>>(r, g->V, nchunks, den.mask, den.rho, counts, list);
+    ctx->launches += 3;
+    unsigned total = 0;
+    SHL_CUDA(ctx, cudaMemcpyAsync(&total, counts + nb, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    g->list = list;
+    g->chunks = total;
+    g->bpk = vec_bpk(total);
+    return SHL_OK;
+}
+
 // Apply grid CTAs per load case (the deferred p.q partials of one case).
 template <typename T>
 inline int apply_ctas_per_case(int r, const Density &den) {
@@ -1239,7 +1261,8 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             // one iteration: q = K p (+ p.q -> alpha); x, r update (+ r.r, and
             // the first fine pre-smoothing step z = w D^-1 r); V-cycle; last
             // fine post-smoothing step (+ r.z -> beta); p = z + beta p
-            const VecGeom vg = vec_geom<float>(N);
+            VecGeom vg = vec_geom<float>(N);
+            if (o->active && vg.V > 1) SHL_TRY(active_chunk_list(ctx, r, den, &vg, s));
             FineJacobi fj{};
             if (use_mg) fj = FineJacobi{mg.lv[0].Dinv, mg.lv[0].omega, z32};
             auto iteration = [&]() -> int {

@@ -21,25 +21,124 @@ namespace shl {
 constexpr int kVecThreads = 256;
 constexpr int kVecBlocksPerSM = 4;  // register budget 64 per thread: one wave of 6 x bpk blocks
 
-// Launch shape of the vector kernels for n nodes.
+// Launch shape of the vector kernels for n nodes.  With a chunk list (the
+// active set's chunks, ascending) the kernels visit only the listed chunks:
+// the others hold nodes with no active element, whose rows and columns of K
+// and (block-)Jacobi inverses are zero, so nothing there can reach an active
+// node or a dot product.
 struct VecGeom {
     int V = 1;          // elements per chunk (16 bytes, or 1 for ragged sizes)
-    size_t chunks = 0;  // chunks per plane
+    size_t chunks = 0;  // chunks per plane (the loop bound: listed chunks when list != null)
     int bpk = 1;        // blocks per load case
+    const unsigned *list = nullptr;  // chunk indices, or null for all chunks
     int blocks() const { return 6 * bpk; }
+    __host__ __device__ size_t chunk(size_t i) const { return list ? (size_t)list[i] : i; }
 };
+
+inline int vec_bpk(size_t chunks) {
+    size_t b = (chunks + kVecThreads - 1) / kVecThreads;
+    const size_t cap = 148 * kVecBlocksPerSM / 6;  // the whole grid resident at once
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
 
 template <typename T>
 inline VecGeom vec_geom(size_t n) {
     VecGeom g;
     g.V = (n % (16 / sizeof(T)) == 0) ? (int)(16 / sizeof(T)) : 1;
     g.chunks = n / g.V;
-    size_t b = (g.chunks + kVecThreads - 1) / kVecThreads;
-    const size_t cap = 148 * kVecBlocksPerSM / 6;  // the whole grid resident at once
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    g.bpk = (int)b;
+    g.bpk = vec_bpk(g.chunks);
     return g;
+}
+
+// Active chunks of V consecutive nodes (a node is active when one of its 8
+// incident elements has a positive density; den: mask bytes or culled rho),
+// compacted in ascending order: per-block flags and counts, a one-block scan,
+// then an ordered write.  kChunkBlock chunks per block of kVecThreads threads.
+constexpr int kChunkPerThread = 4, kChunkBlock = kVecThreads * kChunkPerThread;
+
+__device__ inline bool chunk_active(int r, int V, const uint8_t *mask, const double *rho, size_t c) {
+    const size_t N = (size_t)r * r * r;
+    for (int e = 0; e < V; ++e) {
+        const size_t n = c * V + e;
+        if (n >= N) return false;
+        const int ix = n % r, iy = (n / r) % r, iz = n / ((size_t)r * r);
+        for (int b = 0; b < 8; ++b) {
+            const size_t el = ((size_t)wrapi(iz - (b >> 2), r) * r + wrapi(iy - ((b >> 1) & 1), r)) * r +
+                              wrapi(ix - (b & 1), r);
+            if (rho ? rho[el] > 0.0 : mask[el] != 0) return true;
+        }
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kVecThreads) chunk_count_kernel(int r, int V, size_t nchunks, const uint8_t *mask,
+                                                                   const double *rho, unsigned *counts) {
+    __shared__ unsigned wsum[kVecThreads / 32];
+    unsigned cnt = 0;
+    for (int u = 0; u < kChunkPerThread; ++u) {
+        const size_t c = (size_t)blockIdx.x * kChunkBlock + threadIdx.x * kChunkPerThread + u;
+        if (c < nchunks && chunk_active(r, V, mask, rho, c)) ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < kVecThreads / 32; ++w) t += wsum[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// One block: counts[b] -> exclusive offsets in place; total into *total.
+__global__ void __launch_bounds__(1024) chunk_scan_kernel(int nb, unsigned *counts, unsigned *total) {
+    __shared__ unsigned carry;
+    __shared__ unsigned wsum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const unsigned v = i < nb ? counts[i] : 0;
+        unsigned x = v;  // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        unsigned before = carry;
+        for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += wsum[w];
+        if (i < nb) counts[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kVecThreads) chunk_write_kernel(int r, int V, size_t nchunks, const uint8_t *mask,
+                                                                   const double *rho, const unsigned *offsets,
+                                                                   unsigned *list) {
+    __shared__ unsigned wsum[kVecThreads / 32];
+    bool f[kChunkPerThread];
+    unsigned cnt = 0;
+    for (int u = 0; u < kChunkPerThread; ++u) {
+        const size_t c = (size_t)blockIdx.x * kChunkBlock + threadIdx.x * kChunkPerThread + u;
+        f[u] = c < nchunks && chunk_active(r, V, mask, rho, c);
+        cnt += f[u];
+    }
+    unsigned x = cnt;  // inclusive scan over the block
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned pos = offsets[blockIdx.x] + x - cnt;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) pos += wsum[w];
+    for (int u = 0; u < kChunkPerThread; ++u)
+        if (f[u]) list[pos++] = (unsigned)((size_t)blockIdx.x * kChunkBlock + threadIdx.x * kChunkPerThread + u);
 }
 
 template <typename T, int V>
@@ -205,8 +304,8 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM)
         T *__restrict__ r = a.r + (size_t)3 * k * N;
         const T *__restrict__ p = a.p + (size_t)3 * k * N;
         const T *__restrict__ q = a.q + (size_t)3 * k * N;
-        for (size_t c = (size_t)j * kVecThreads + threadIdx.x; c < g.chunks; c += (size_t)g.bpk * kVecThreads) {
-            const size_t n0 = c * V;
+        for (size_t ci = (size_t)j * kVecThreads + threadIdx.x; ci < g.chunks; ci += (size_t)g.bpk * kVecThreads) {
+            const size_t n0 = g.chunk(ci) * V;
             Chunk<T, V> rn[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -300,8 +399,8 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM)
         const float *__restrict__ r = a.r + (size_t)3 * k * N;
         const float *__restrict__ tk = t + (size_t)3 * k * N;
         float *__restrict__ z = fj.z + (size_t)3 * k * N;
-        for (size_t c = (size_t)j * kVecThreads + threadIdx.x; c < g.chunks; c += (size_t)g.bpk * kVecThreads) {
-            const size_t n0 = c * V;
+        for (size_t ci = (size_t)j * kVecThreads + threadIdx.x; ci < g.chunks; ci += (size_t)g.bpk * kVecThreads) {
+            const size_t n0 = g.chunk(ci) * V;
             Chunk<float, V> rv[3], dv[3], zv[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -370,8 +469,8 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSM) vec_direction_ke
     T *__restrict__ p = a.p + (size_t)3 * k * N;
     const T *__restrict__ r = a.r + (size_t)3 * k * N;
     const T *__restrict__ z = a.z ? a.z + (size_t)3 * k * N : nullptr;
-    for (size_t c = (size_t)j * kVecThreads + threadIdx.x; c < g.chunks; c += (size_t)g.bpk * kVecThreads) {
-        const size_t n0 = c * V;
+    for (size_t ci = (size_t)j * kVecThreads + threadIdx.x; ci < g.chunks; ci += (size_t)g.bpk * kVecThreads) {
+        const size_t n0 = g.chunk(ci) * V;
         Chunk<T, V> di;
         if (!z) di = ldc<T, V>(a.dinv + n0);
 #pragma unroll
