@@ -142,3 +142,36 @@ def test_fresh_contexts_on_threads_agree(gpu):
         assert not isinstance(o, Exception), o
         C, st = o
         assert st["iters"] == stref["iters"] and np.array_equal(C, Cref)
+
+
+def test_served_golden_designs_match_oracle(gpu):
+    """Designs whose C^H the oracle has fixed (tests/golden), served inside a
+    concurrent mix of other sizes: each served C^H against the oracle's value
+    (entry error <= 1e-9 at tol 1e-10), the ersatz void and the active set."""
+    import json
+    import os
+    gold_dir = os.path.join(os.path.dirname(__file__), "golden")
+
+    def gold(name):
+        with open(os.path.join(gold_dir, name + ".json")) as f:
+            return np.array(json.load(f)["C"])
+
+    def entry_err(C, Cref):
+        s = np.abs(Cref).max()
+        return np.max(np.abs(C - Cref) / np.maximum(np.abs(Cref), 1e-2 * s))
+
+    probes = [(inputs.plain_32(0), 32, _opts(), gold("plain32_s0")),
+              (inputs.gaussian_64(0), 64, _opts(), gold("gaussian64_s0")),
+              (inputs.plain_32(0), 32, _opts(active=1), gold("plain32_s0_active"))]
+    with shl.Context(0, max_batch=8) as c:
+        tickets = []
+        for i, (d, r, o, g) in enumerate(probes):
+            tickets.append(shl.shl_serve_submit(c.handle, d, r, o))
+            for j in range(2):  # other sizes arriving around each probe
+                tickets.append(shl.shl_serve_submit(c.handle, inputs.random_design(200 + 2 * i + j, 12, 0.1),
+                                                    (24, 40)[j], _opts()))
+        res = {tk: shl.shl_serve_wait(c.handle, tk) for tk in tickets}
+        for k, (d, r, o, g) in enumerate(probes):
+            out = res[tickets[3 * k]]
+            assert out["stats"]["status"] == 0
+            assert entry_err(out["C"], g) <= 1e-9
