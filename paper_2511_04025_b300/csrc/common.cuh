@@ -55,6 +55,9 @@ struct shl_ctx {
     // would disturb other slots' CUDA-graph captures)
     bool stream_ordered_alloc = false;
     void *pinned = nullptr;  // host staging of the multigrid setup (page-locked, allocated once)
+    // instantiated PCG-iteration graphs by solve shape, refreshed per solve with
+    // cudaGraphExecUpdate (an instantiation costs far more than an update)
+    std::map<std::string, cudaGraphExec_t> graphs;
 };
 
 namespace shl {
@@ -132,6 +135,9 @@ inline int ws_get_t(shl_ctx *ctx, const std::string &name, size_t count, T **out
 }
 
 inline void ws_free_all(shl_ctx *ctx) {
+    for (auto &kv : ctx->graphs)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
     for (auto &kv : ctx->ws.slots)
         if (kv.second.first) {
             if (ctx->stream_ordered_alloc)

@@ -505,17 +505,21 @@ inline const char *numeric_err_text(int code) {
 
 struct IterGraph {
     cudaGraphExec_t exec = nullptr;
+    bool owned = true;                // false: the context's graph cache owns exec
     unsigned long long launches = 0;  // kernels per replay
     std::function<int()> direct;      // fallback: launch the iteration's kernels
     ~IterGraph() {
-        if (exec) cudaGraphExecDestroy(exec);
+        if (exec && owned) cudaGraphExecDestroy(exec);
     }
 };
 
 // Records one iteration; if capture or instantiation fails, the iteration is
 // replayed by launching its kernels directly (same work, more host time).
+// With a key, the instantiated graph is kept in the context and later solves
+// of the same shape update it in place with the newly captured parameters
+// (instantiated again only if the update is refused).
 template <typename F>
-inline int capture_iteration(shl_ctx *ctx, cudaStream_t s, IterGraph *g, F &&record) {
+inline int capture_iteration(shl_ctx *ctx, cudaStream_t s, IterGraph *g, F &&record, const std::string &key = "") {
     g->direct = [record]() mutable { return record(); };
     const unsigned long long l0 = ctx->launches;
     cudaGraph_t graph = nullptr;
@@ -537,6 +541,26 @@ inline int capture_iteration(shl_ctx *ctx, cudaStream_t s, IterGraph *g, F &&rec
     if (rc != SHL_OK) {
         cudaGraphDestroy(graph);
         return rc;
+    }
+    if (!key.empty()) {
+        cudaGraphExec_t &cached = ctx->graphs[key];
+        if (cached) {
+            cudaGraphExecUpdateResultInfo info{};
+            if (cudaGraphExecUpdate(cached, graph, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(cached);
+                cached = nullptr;
+            }
+        }
+        if (!cached && cudaGraphInstantiate(&cached, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cached = nullptr;
+        }
+        cudaGraphDestroy(graph);
+        g->exec = cached;
+        g->owned = false;
+        g->launches = per_iter;
+        return SHL_OK;
     }
     const cudaError_t e2 = cudaGraphInstantiate(&g->exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -669,7 +693,7 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
                              s);
         launch_vec_direction<T>(ctx, va, vg, s);
         return SHL_OK;
-    }));
+    }, "pcg" + std::to_string(sizeof(T)) + "_" + std::to_string(r)));
     // the device deactivates every load case by st->maxit; the host cap is a backstop
     const long long cap = (long long)max_iters_backstop + 2 * chunk;
     for (long long it = 0;; it += chunk) {
@@ -1277,7 +1301,8 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                 return SHL_OK;
             };
             IterGraph graph;
-            SHL_TRY(capture_iteration(ctx, s, &graph, iteration));
+            SHL_TRY(capture_iteration(ctx, s, &graph, iteration,
+                                      "pcg32_" + std::to_string(r) + (use_mg ? "_mg" : "_jacobi")));
             PcgState hst;
             for (long long it = 0;; it += chunk) {
                 if (it > (long long)maxit + 2 * chunk)
