@@ -242,11 +242,15 @@ def time_apply(h, r, design, stream, launches=40):
     return a0.elapsed_time(a1) / 1e3 / launches
 
 
+ROW_GRIDS = (32, 48, 64, 96, 128, 256)  # grids the FP32 row kernel serves (others: the tile kernel)
+
+
 def apply_roofline(r, apply_s):
     peak, peak_kind = peaks()
     achieved = APPLY_BYTES_PER_NODE_F32 * r ** 3 / apply_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": "apply_rows_kernel<64> (FP32 stiffness apply)" if r in (32, 64, 128, 256) else "apply_kernel<float> (FP32 stiffness apply)",
+            "traffic": APPLY_TRAFFIC_64 if r == 64 else None, "kernel": (f"apply_rows_kernel<{r}> (FP32 stiffness apply)" if r in ROW_GRIDS
+                       else "apply_kernel<float> (FP32 stiffness apply)"),
             "peak_kind": peak_kind, "launch_us": apply_s * 1e6, "operands": "HBM (rotating > L2)"}
 
 

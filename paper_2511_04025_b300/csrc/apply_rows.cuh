@@ -1,7 +1,8 @@
 // apply_rows.cuh -- FP32 matrix-free stiffness apply q = K p (six load cases,
 // Eq. inv-design cell problems; Sec. 4.2.2: finest level on the fly, all
 // right-hand sides in one launch, converged right-hand sides skipped) for the
-// grids whose rows split evenly into warp segments: r = 32, 64, 128, 256.
+// grids r = 32, 48, 64, 96, 128, 256 (any multiple of 16 works: a row's pairs
+// fill a group of 16 lanes or of whole warps, the rest of the group pads).
 // Other grids, and the FP64 / double-float kinds, use apply_kernel
 // (apply.cuh); both compute the same operator.
 //
@@ -21,8 +22,9 @@
 //    its closed form (below) scaled by the two moduli, and transforms back;
 //  - the +z half of the result is carried in registers to the next plane;
 //    the +x corner goes to the next thread of the row by a warp shuffle
-//    (the row is periodic: it wraps within the warp, or through shared
-//    memory when a row spans several warps); the +y corner row goes to the
+//    (the row is periodic: it wraps within the lane group, or through shared
+//    memory when a row spans several warps); padding lanes compute on a copy
+//    of the row's last pair and write nothing; the +y corner row goes to the
 //    next element row through shared memory (one barrier per plane).
 // Deterministic, no atomics.
 //
@@ -170,8 +172,19 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 #ifndef SHL_ROWS_ZUNROLL
 #define SHL_ROWS_ZUNROLL 2
 #endif
+#ifndef SHL_ROWS_TY48
+#define SHL_ROWS_TY48 8
+#endif
+#ifndef SHL_ROWS_TY96
+#define SHL_ROWS_TY96 7
+#endif
 __host__ __device__ constexpr int rows_ty_of(int r) {
-    return r == 32 ? SHL_ROWS_TY32 : (r == 64 ? SHL_ROWS_TY64 : (r == 128 ? SHL_ROWS_TY128 : SHL_ROWS_TY256));
+    return r == 32    ? SHL_ROWS_TY32
+           : r == 48  ? SHL_ROWS_TY48
+           : r == 64  ? SHL_ROWS_TY64
+           : r == 96  ? SHL_ROWS_TY96
+           : r == 128 ? SHL_ROWS_TY128
+                      : SHL_ROWS_TY256;
 }
 __host__ __device__ constexpr int rows_minb_of(int r) {
     return r == 32 ? SHL_ROWS_MINB32 : (r == 64 ? SHL_ROWS_MINB64 : (r == 128 ? SHL_ROWS_MINB128 : SHL_ROWS_MINB256));
@@ -179,18 +192,21 @@ __host__ __device__ constexpr int rows_minb_of(int r) {
 
 template <int R>
 struct RowShape {
-    static_assert(R == 32 || R == 64 || R == 128 || R == 256, "row apply: r must be 32, 64, 128 or 256");
+    // rows of 16-byte multiples for the bulk copies of the mask rows; one row's
+    // element pairs fill a lane group of 16 lanes or whole warps
+    static_assert(R % 16 == 0 && R >= 32 && R <= 256, "row apply: r must be a multiple of 16 in [32, 256]");
     static constexpr int TY = rows_ty_of(R);
     // TY need not divide r: the last tile's rows past the grid wrap around,
     // are computed and not stored
     static_assert(TY >= 1 && TY + 2 <= R, "row apply: 1 <= TY <= r - 2");
     static constexpr int MINB = rows_minb_of(R);
-    static constexpr int P = R / 2;                // element pairs (threads) per row
+    static constexpr int P = R / 2;                // element pairs per row
+    static constexpr int LPR = P <= 16 ? 16 : (P + 31) / 32 * 32;  // lanes per row (the last P..LPR-1 pad)
     static constexpr int NR = TY + 1;              // element rows, row 0 = halo
     static constexpr int NYR = TY + 2;             // node rows per plane
-    static constexpr int LIVE = NR * P;            // threads with an element pair
+    static constexpr int LIVE = NR * LPR;          // threads with a row slot
     static constexpr int THREADS = (LIVE + 31) / 32 * 32;
-    static constexpr int S = P > 32 ? P / 32 : 1;  // warps per row
+    static constexpr int S = LPR >= 32 ? LPR / 32 : 1;  // warps per row
     static constexpr int PD = SHL_ROWS_PD;         // planes copied ahead of use
     static constexpr int NSLOT = PD + 1;           // ring slots
     static constexpr int NODE_BYTES = 3 * NYR * R * 4;
@@ -246,12 +262,15 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
 
     if (act) {
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-        const bool live = tid < Sh::LIVE;
-        const int i = live ? tid / P : NR - 1;  // element row (idle threads shadow the last row, write nothing)
-        const int jp = live ? tid % P : 0;      // element pair
+        constexpr int LPR = Sh::LPR;
+        const bool slot_ok = tid < Sh::LIVE;
+        const int jl = slot_ok ? tid % LPR : 0;  // lane within the row's lane group
+        const bool live = slot_ok && jl < P;     // holds an element pair (padding lanes write nothing)
+        const int i = slot_ok ? tid / LPR : NR - 1;  // element row (idle threads shadow the last row)
+        const int jp = live ? jl : P - 1;        // element pair (padding lanes shadow the last pair)
         const int x = 2 * jp;
-        const int xn = (x + 2) & (R - 1);       // node x + 2, periodic
-        const int seg = jp / 32;
+        const int xn = x + 2 == R ? 0 : x + 2;   // node x + 2, periodic
+        const int seg = jl / 32;
         const size_t N = (size_t)R * R * R;
         const int y0 = blockIdx.x * TY;
         const int z0 = (int)(blockIdx.y * R) / a.zc, tz = (int)((blockIdx.y + 1) * R) / a.zc - z0;
@@ -340,8 +359,12 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
         wait_plane(0);
         face(0, ftb);
 
-        const int src_lane = P >= 32 ? ((lane + 31) & 31) : ((lane & ~(P - 1)) | ((lane + P - 1) & (P - 1)));
-        const bool patch = (S > 1) && live && (lane == 0);  // the row's left neighbour is in another warp
+        // the left neighbour pair's lane (the row is periodic: pair 0's is pair P - 1);
+        // across warps (S > 1) lane 0 takes it from the previous warp's spill word
+        const int src_lane = S > 1 ? ((lane + 31) & 31)
+                                   : ((lane & ~(LPR - 1)) + (jl == 0 ? P - 1 : jl - 1));
+        const bool patch = (S > 1) && live && (lane == 0);
+        const int last_lane = S > 1 ? min(31, P - 1 - 32 * seg) : 31;  // this warp's last pair
         const int segm1 = (seg + S - 1) % S;
 
         // unrolled by two: the face arrays alternate roles between the copies
@@ -438,7 +461,7 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
                     const float2 ot = p2add(W[c][2], make_float2(patch ? 0.f : rb3[c], W[c][3].x));
                     *reinterpret_cast<float2 *>(yt + c * R + x) = ot;
                 }
-                if (S > 1 && lane == 31) {
+                if (S > 1 && lane == last_lane) {
                     float *sp = spill + ((size_t)((par * NR + i) * S + seg) * 2) * 3;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {

@@ -109,9 +109,9 @@ inline int apply_zc(int r, int nvec) {
 }
 
 // ---------------------------------------------------------------------------
-// Row apply (apply_rows.cuh): FP32, r = 32, 64, 128, 256
+// Row apply (apply_rows.cuh): FP32, r = 32, 48, 64, 96, 128, 256
 // ---------------------------------------------------------------------------
-inline bool rows_grid(int r) { return r == 32 || r == 64 || r == 128 || r == 256; }
+inline bool rows_grid(int r) { return r == 32 || r == 48 || r == 64 || r == 96 || r == 128 || r == 256; }
 inline int rows_ty(int r) { return rows_ty_of(r); }
 
 // Shared-memory opt-in and resident CTAs per SM of one row-apply kernel on
@@ -141,7 +141,9 @@ inline int rows_prepare() {
 inline int rows_occupancy(int r, bool smooth) {
     switch (r) {
         case 32: return smooth ? rows_prepare<32, true>() : rows_prepare<32, false>();
+        case 48: return smooth ? rows_prepare<48, true>() : rows_prepare<48, false>();
         case 64: return smooth ? rows_prepare<64, true>() : rows_prepare<64, false>();
+        case 96: return smooth ? rows_prepare<96, true>() : rows_prepare<96, false>();
         case 128: return smooth ? rows_prepare<128, true>() : rows_prepare<128, false>();
         case 256: return smooth ? rows_prepare<256, true>() : rows_prepare<256, false>();
     }
@@ -206,9 +208,17 @@ inline int launch_apply_rows(shl_ctx *ctx, ApplyArgs<T> a, const ApplyGeom &geo,
                 if (sm) pdl_launch(apply_rows_kernel<32, true>, g, RowShape<32>::THREADS, RowShape<32>::smem<true>(), s, a, kc);
                 else pdl_launch(apply_rows_kernel<32, false>, g, RowShape<32>::THREADS, RowShape<32>::smem<false>(), s, a, kc);
                 break;
+            case 48:
+                if (sm) pdl_launch(apply_rows_kernel<48, true>, g, RowShape<48>::THREADS, RowShape<48>::smem<true>(), s, a, kc);
+                else pdl_launch(apply_rows_kernel<48, false>, g, RowShape<48>::THREADS, RowShape<48>::smem<false>(), s, a, kc);
+                break;
             case 64:
                 if (sm) pdl_launch(apply_rows_kernel<64, true>, g, RowShape<64>::THREADS, RowShape<64>::smem<true>(), s, a, kc);
                 else pdl_launch(apply_rows_kernel<64, false>, g, RowShape<64>::THREADS, RowShape<64>::smem<false>(), s, a, kc);
+                break;
+            case 96:
+                if (sm) pdl_launch(apply_rows_kernel<96, true>, g, RowShape<96>::THREADS, RowShape<96>::smem<true>(), s, a, kc);
+                else pdl_launch(apply_rows_kernel<96, false>, g, RowShape<96>::THREADS, RowShape<96>::smem<false>(), s, a, kc);
                 break;
             case 128:
                 if (sm) pdl_launch(apply_rows_kernel<128, true>, g, RowShape<128>::THREADS, RowShape<128>::smem<true>(), s, a, kc);

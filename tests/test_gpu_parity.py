@@ -117,7 +117,7 @@ def _rand_mask(r, seed, frac=0.3):
     return (np.random.default_rng(seed).uniform(size=r ** 3) < frac).astype(np.uint8)
 
 
-@pytest.mark.parametrize("r", [2, 3, 5, 16, 20, 32, 33, 64])
+@pytest.mark.parametrize("r", [2, 3, 5, 16, 20, 32, 33, 48, 64])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_apply_matches_assembled_oracle(ctx, r, dtype):
     m = _rand_mask(r, r)
@@ -146,10 +146,11 @@ def test_apply_smooth_density_and_subset_of_load_cases(ctx):
     assert np.abs(oracle.soa_to_aos(q.cpu().numpy()) - y).max() <= 1e-12 * np.abs(y).max()
 
 
-def test_apply_rows_smooth_density_matches_oracle(ctx):
-    """FP32 apply at r = 64 (the row kernel) with the smoothed density and a
-    subset of load cases, against the assembled oracle."""
-    r = 64
+@pytest.mark.parametrize("r", [48, 64])
+def test_apply_rows_smooth_density_matches_oracle(ctx, r):
+    """FP32 apply at r = 48 (row lane groups with padding lanes) and r = 64
+    (the row kernel) with the smoothed density and a subset of load cases,
+    against the assembled oracle."""
     rho = np.random.default_rng(17).uniform(size=r ** 3)
     x = np.random.default_rng(18).standard_normal((3, r ** 3, 3))
     y = oracle.apply(r, rho, x, E=1.0, nu=0.3, Evoid=1e-6)
@@ -160,9 +161,9 @@ def test_apply_rows_smooth_density_matches_oracle(ctx):
     assert np.abs(oracle.soa_to_aos(q.double().cpu().numpy()) - y).max() <= 2e-6 * np.abs(y).max()
 
 
-@pytest.mark.parametrize("r", [32, 64, 128, 256])
+@pytest.mark.parametrize("r", [32, 48, 64, 96, 128, 256])
 def test_apply_row_kernel_matches_tile_kernel(ctx, r):
-    """The FP32 row kernel (r = 32, 64, 128, 256: density rows 16-byte aligned)
+    """The FP32 row kernel (r = 32, 48, 64, 96, 128, 256; density rows 16-byte aligned)
     against the tile kernel on the same operands (the tile kernel serves a
     density buffer that starts one byte past a 16-byte boundary), every load
     case, with a ragged mix of solid and void."""
