@@ -138,18 +138,21 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 // Output node rows per CTA (TY) and resident CTAs per SM the registers are
 // budgeted for (MINB), per grid size.  A CTA's warps spread over the SM's four
 // schedulers, whose register files bound the registers per thread; the
-// per-plane barrier makes the scheduler with the most warps set the pace.
-// Measured on B300 (us per launch): r = 64: TY 8 (9 warps) 22.4, 7 (8 warps)
-// 26.2, 15 (16 warps) 22.8; r = 128: TY 3 (8 warps) 174, 4 (10) 163, 7 (16,
-// 124 registers) 138; r = 256: TY 2 (12 warps) 1256, 3 (16) 1110.
+// per-plane barrier makes the scheduler with the most warps set the pace, so
+// the warps per CTA are best a multiple of four, with the CTAs of all load
+// cases filling the 148 SMs.  Measured on B300 (us per launch): r = 32: TY 8
+// (5 warps) 6.45, 11 (6 warps, 2 CTAs per SM) 5.48; r = 64: TY 7 (8 warps)
+// 26.2, 8 (9 warps) 22.2, 11 (12 warps, 6 x 4 x 6 = 144 CTAs) 18.1, 15 (16
+// warps) 22.8; r = 128: TY 3 (8 warps) 174, 4 (10) 163, 5 (12) 153, 7 (16)
+// 139; r = 256: TY 2 (12 warps) 1248, 3 (16) 1116.
 #ifndef SHL_ROWS_TY32
-#define SHL_ROWS_TY32 8
+#define SHL_ROWS_TY32 11
 #endif
 #ifndef SHL_ROWS_MINB32
 #define SHL_ROWS_MINB32 1
 #endif
 #ifndef SHL_ROWS_TY64
-#define SHL_ROWS_TY64 8
+#define SHL_ROWS_TY64 11
 #endif
 #ifndef SHL_ROWS_MINB64
 #define SHL_ROWS_MINB64 1
@@ -237,9 +240,14 @@ __device__ __forceinline__ float2 pair_modulus(const unsigned char *den_row, int
     }
 }
 
-template <int R, bool SMOOTH>
+// DOT: the fused reduction, fixed per instantiation (a.dot must match): 0
+// none, 1 p.q (q.q, mode 2, is left to the tile kernel, which serves the
+// residual applies that use it).  Launched with exactly RowShape<R>::THREADS
+// threads.
+template <int R, bool SMOOTH, int DOT>
 __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     apply_rows_kernel(const ApplyArgs<float> a, const RowConsts kc) {
+    static_assert(DOT == 0 || DOT == 1, "row apply: DOT is 0 or 1");
     pdl_enter();
     using Sh = RowShape<R>;
     constexpr int TY = Sh::TY, P = Sh::P, NR = Sh::NR, NYR = Sh::NYR, S = Sh::S, PD = Sh::PD, NSLOT = Sh::NSLOT;
@@ -263,9 +271,11 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     if (act) {
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         constexpr int LPR = Sh::LPR;
-        const bool slot_ok = tid < Sh::LIVE;
+        // every thread holds a pair when the rows fill the CTA exactly (no padding)
+        constexpr bool kFull = Sh::LIVE == Sh::THREADS && LPR == P;
+        const bool slot_ok = kFull || tid < Sh::LIVE;
         const int jl = slot_ok ? tid % LPR : 0;  // lane within the row's lane group
-        const bool live = slot_ok && jl < P;     // holds an element pair (padding lanes write nothing)
+        const bool live = kFull || (slot_ok && jl < P);  // holds an element pair (padding lanes write nothing)
         const int i = slot_ok ? tid / LPR : NR - 1;  // element row (idle threads shadow the last row)
         const int jp = live ? jl : P - 1;        // element pair (padding lanes shadow the last pair)
         const int x = 2 * jp;
@@ -391,10 +401,10 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
             // y[c][0] are zero)
             // E-scaled constants: scalar products with the parameter-bank values
             // (no registers held for the constants)
-            const float2 eA = make_float2(Ee.x * kc.amb, Ee.y * kc.amb), eB = make_float2(Ee.x * kc.b, Ee.y * kc.b),
-                         eP = make_float2(Ee.x * kc.p, Ee.y * kc.p), eQ = make_float2(Ee.x * kc.q, Ee.y * kc.q),
-                         eF = make_float2(Ee.x * kc.f, Ee.y * kc.f), eR = make_float2(Ee.x * kc.rr, Ee.y * kc.rr),
-                         eD = make_float2(Ee.x * kc.d, Ee.y * kc.d);
+            const float2 eA = p2mul(Ee, p2splat(kc.amb)), eB = p2mul(Ee, p2splat(kc.b)),
+                         eP = p2mul(Ee, p2splat(kc.p)), eQ = p2mul(Ee, p2splat(kc.q)),
+                         eF = p2mul(Ee, p2splat(kc.f)), eR = p2mul(Ee, p2splat(kc.rr)),
+                         eD = p2mul(Ee, p2splat(kc.d));
             float2 y[3][8];
             {  // c = 0: (u01, u12, u24) -> (y01, y12, y24)
                 const float2 t0 = p2mul(eB, p2add(p2add(u[0][1], u[1][2]), u[2][4]));
@@ -485,9 +495,10 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
                 const int ny = y0 - 1 + i;  // node row (inside the tile and the grid)
                 const size_t nrow = ((size_t)ez * R + ny) * R + x;
                 float *qrow = a.q + (size_t)(3 * k) * N + nrow;
-                const bool pin_here = a.pin && nrow == 0;
+                const bool pin_here = a.pin && ez == 0 && ny == 0 && x == 0;
                 // p at the pair's own nodes (x, x + 1) of node row i, bottom plane s (for p.q)
                 const float *own = reinterpret_cast<const float *>(smraw + (s % NSLOT) * SLOT) + i * R + x;
+                float2 v = make_float2(0.f, 0.f);  // this plane's three products (per element of the pair)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float2 otp = *reinterpret_cast<const float2 *>(ytp + c * R + x);
@@ -499,14 +510,16 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
                     float2 qv = p2add(p2add(W[c][0], make_float2(recv1, W[c][1].x)), otp);
                     if (pin_here) qv.x = 0.f;
                     *reinterpret_cast<float2 *>(qrow + (size_t)c * N) = qv;
-                    if (a.dot) {  // packed compensated sum
-                        const float2 v =
-                            a.dot == 1 ? p2mul(qv, *reinterpret_cast<const float2 *>(own + c * NYR * R)) : p2mul(qv, qv);
-                        const float2 yv = p2sub(v, dc);
-                        const float2 tv = p2add(ds, yv);
-                        dc = p2sub(p2sub(tv, ds), yv);
-                        ds = tv;
+                    if constexpr (DOT != 0) {
+                        const float2 w = *reinterpret_cast<const float2 *>(own + c * NYR * R);
+                        v = c == 0 ? p2mul(qv, w) : p2fma(qv, w, v);
                     }
+                }
+                if constexpr (DOT != 0) {  // one packed compensated add per plane
+                    const float2 yv = p2sub(v, dc);
+                    const float2 tv = p2add(ds, yv);
+                    dc = p2sub(p2sub(tv, ds), yv);
+                    ds = tv;
                 }
             }
 #pragma unroll
@@ -518,7 +531,7 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
         // every plane issued was waited for in the loop; nothing is in flight
     }
 
-    if (!a.dot) return;
+    if constexpr (DOT == 0) return;
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     // this thread's two compensated halves as one double-float, then the CTA's

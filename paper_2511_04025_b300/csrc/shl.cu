@@ -126,14 +126,19 @@ inline int rows_prepare() {
     std::lock_guard<std::mutex> lk(mu);
     if (occ[dev] == 0) {
         const size_t sm = RowShape<R>::template smem<SMOOTH>();
-        int n = 0;
-        if (cudaFuncSetAttribute(apply_rows_kernel<R, SMOOTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        int n = 0, n0 = 0;
+        if (cudaFuncSetAttribute(apply_rows_kernel<R, SMOOTH, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_rows_kernel<R, SMOOTH>, RowShape<R>::THREADS,
+            cudaFuncSetAttribute(apply_rows_kernel<R, SMOOTH, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, apply_rows_kernel<R, SMOOTH, 0>,
+                                                          RowShape<R>::THREADS, sm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_rows_kernel<R, SMOOTH, 1>, RowShape<R>::THREADS,
                                                           sm) != cudaSuccess) {
             cudaGetLastError();
             n = 0;
         }
+        n = std::min(n, n0);  // one geometry (and partials layout) for both DOT variants
         occ[dev] = n > 0 ? n : -1;
     }
     return occ[dev];
@@ -184,6 +189,23 @@ inline ApplyGeom apply_geom(int r, int nvec, const uint8_t *mask, const double *
     return ApplyGeom{((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY), apply_zc<T>(r, nvec), 0};
 }
 
+template <int R, bool SMOOTH>
+inline void rows_launch(dim3 g, cudaStream_t s, const ApplyArgs<float> &a, const RowConsts &kc) {
+    constexpr int NT = RowShape<R>::THREADS;
+    const size_t sm = RowShape<R>::template smem<SMOOTH>();
+    if (a.dot == 1)
+        pdl_launch(apply_rows_kernel<R, SMOOTH, 1>, g, NT, sm, s, a, kc);
+    else
+        pdl_launch(apply_rows_kernel<R, SMOOTH, 0>, g, NT, sm, s, a, kc);
+}
+template <int R>
+inline void rows_launch_r(dim3 g, cudaStream_t s, const ApplyArgs<float> &a, const RowConsts &kc) {
+    if (a.rho)
+        rows_launch<R, true>(g, s, a, kc);
+    else
+        rows_launch<R, false>(g, s, a, kc);
+}
+
 template <typename T>
 inline int launch_apply_rows(shl_ctx *ctx, ApplyArgs<T> a, const ApplyGeom &geo, cudaStream_t s) {
     if constexpr (!std::is_same<T, float>::value) {
@@ -202,32 +224,13 @@ inline int launch_apply_rows(shl_ctx *ctx, ApplyArgs<T> a, const ApplyGeom &geo,
         if (!a.err) SHL_TRY(ws_get_t(ctx, "apply_err", 1, &a.err));
         a.zc = geo.gy;
         const dim3 g(geo.gx, geo.gy, a.nvec);
-        const bool sm = a.rho != nullptr;
         switch (a.r) {
-            case 32:
-                if (sm) pdl_launch(apply_rows_kernel<32, true>, g, RowShape<32>::THREADS, RowShape<32>::smem<true>(), s, a, kc);
-                else pdl_launch(apply_rows_kernel<32, false>, g, RowShape<32>::THREADS, RowShape<32>::smem<false>(), s, a, kc);
-                break;
-            case 48:
-                if (sm) pdl_launch(apply_rows_kernel<48, true>, g, RowShape<48>::THREADS, RowShape<48>::smem<true>(), s, a, kc);
-                else pdl_launch(apply_rows_kernel<48, false>, g, RowShape<48>::THREADS, RowShape<48>::smem<false>(), s, a, kc);
-                break;
-            case 64:
-                if (sm) pdl_launch(apply_rows_kernel<64, true>, g, RowShape<64>::THREADS, RowShape<64>::smem<true>(), s, a, kc);
-                else pdl_launch(apply_rows_kernel<64, false>, g, RowShape<64>::THREADS, RowShape<64>::smem<false>(), s, a, kc);
-                break;
-            case 96:
-                if (sm) pdl_launch(apply_rows_kernel<96, true>, g, RowShape<96>::THREADS, RowShape<96>::smem<true>(), s, a, kc);
-                else pdl_launch(apply_rows_kernel<96, false>, g, RowShape<96>::THREADS, RowShape<96>::smem<false>(), s, a, kc);
-                break;
-            case 128:
-                if (sm) pdl_launch(apply_rows_kernel<128, true>, g, RowShape<128>::THREADS, RowShape<128>::smem<true>(), s, a, kc);
-                else pdl_launch(apply_rows_kernel<128, false>, g, RowShape<128>::THREADS, RowShape<128>::smem<false>(), s, a, kc);
-                break;
-            case 256:
-                if (sm) pdl_launch(apply_rows_kernel<256, true>, g, RowShape<256>::THREADS, RowShape<256>::smem<true>(), s, a, kc);
-                else pdl_launch(apply_rows_kernel<256, false>, g, RowShape<256>::THREADS, RowShape<256>::smem<false>(), s, a, kc);
-                break;
+            case 32: rows_launch_r<32>(g, s, a, kc); break;
+            case 48: rows_launch_r<48>(g, s, a, kc); break;
+            case 64: rows_launch_r<64>(g, s, a, kc); break;
+            case 96: rows_launch_r<96>(g, s, a, kc); break;
+            case 128: rows_launch_r<128>(g, s, a, kc); break;
+            case 256: rows_launch_r<256>(g, s, a, kc); break;
             default:
                 return set_err(ctx, SHL_EINVAL, "internal: row apply for r=%d", a.r);
         }
@@ -243,7 +246,7 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
     ApplyGeom geo = apply_geom<T>(a.r, a.nvec, a.mask, a.rho);
     if (geo.rows) {
         // the bulk row copies need 16-byte aligned rows of p, the paired stores 8-byte aligned q
-        const bool ok = !a.resid && a.p && (reinterpret_cast<uintptr_t>(a.p) & 15) == 0 &&
+        const bool ok = !a.resid && (a.dot == 0 || a.dot == 1) && a.p && (reinterpret_cast<uintptr_t>(a.p) & 15) == 0 &&
                         (reinterpret_cast<uintptr_t>(a.q) & 7) == 0;
         if (!ok && a.dot && a.defer)
             return set_err(ctx, SHL_EINVAL, "internal: deferred apply partials need aligned p and q");
