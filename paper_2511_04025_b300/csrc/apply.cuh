@@ -63,7 +63,7 @@ struct ApplyArgs {
     unsigned *ticket;      // last-block counter
     double *dot_out;       // 6 sums (may be null)
     PcgState *st;          // PCG mode: active flags in, alpha = rz / pq out
-    const int *active_in;  // per load-case flags when st == null (may be null)
+    const int *active_in;  // six per load-case flags when st == null (may be null)
     int case_mask;         // bit k: load case k is computed (others: output and dot left untouched)
     int vec_ok;            // p is 16-byte aligned and r is a multiple of 16 / sizeof(T)
     unsigned *err;         // device error bits (apply_rows.cuh), or null

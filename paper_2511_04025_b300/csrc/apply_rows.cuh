@@ -6,16 +6,16 @@
 // Other grids, and the FP64 / double-float kinds, use apply_kernel
 // (apply.cuh); both compute the same operator.
 //
-// Work split.  A CTA owns one load case, TY node rows (y) over the whole
-// periodic x extent and a chunk of node planes (z).  Its threads form TY + 1
-// element rows (row 0 is the halo row just below the tile); in a row, thread
-// j holds the x-adjacent element pair (2j, 2j+1) and computes both elements
-// at once with packed FP32 pairs (one f32x2 instruction per two elements).
-// The CTA marches along z:
+// Work split.  A CTA takes TY node rows (y) over the whole periodic x extent
+// and a run of node planes (z) of one load case at a time (see the kernel).
+// Its threads form TY + 1 element rows (row 0 is the halo row just below the
+// tile); in a row, thread j holds the x-adjacent element pair (2j, 2j+1) and
+// computes both elements at once with packed FP32 pairs (one f32x2
+// instruction per two elements).  The CTA marches along z:
 //  - the node rows (and density rows) of every plane arrive by bulk
-//    asynchronous copies, one per row, issued by one warp several planes
-//    ahead into a ring of shared-memory slots; each slot has an mbarrier
-//    that counts the bytes landed;
+//    asynchronous copies (one per component and contiguous run of rows),
+//    issued by one warp several planes ahead into a ring of shared-memory
+//    slots; each slot has an mbarrier that counts the bytes landed;
 //  - per plane a thread transforms the top face of its two elements
 //    (Walsh-Hadamard over x and y), combines it with the bottom face kept in
 //    registers from the previous plane (z), applies the element operator in
@@ -169,9 +169,21 @@ constexpr unsigned kApplyErrWaitTimeout = 1u;
 #ifndef SHL_ROWS_MINB256
 #define SHL_ROWS_MINB256 1
 #endif
+// Planes in flight ahead of use (PD) per grid size: measured on B300 (us),
+// r = 64: PD 2 29.2, 3 17.8, 4 16.9, 5 17.0, 6 17.5; r = 128: 3 121.4, 4
+// 119.9; r = 256: 3 1021, 4 1037; r = 32: 3 5.37, 4 5.48.
 #ifndef SHL_ROWS_PD
 #define SHL_ROWS_PD 3
 #endif
+#ifndef SHL_ROWS_PD64
+#define SHL_ROWS_PD64 4
+#endif
+#ifndef SHL_ROWS_PD128
+#define SHL_ROWS_PD128 4
+#endif
+__host__ __device__ constexpr int rows_pd_of(int r) {
+    return r == 64 ? SHL_ROWS_PD64 : (r == 128 ? SHL_ROWS_PD128 : SHL_ROWS_PD);
+}
 #ifndef SHL_ROWS_ZUNROLL
 #define SHL_ROWS_ZUNROLL 2
 #endif
@@ -210,7 +222,7 @@ struct RowShape {
     static constexpr int LIVE = NR * LPR;          // threads with a row slot
     static constexpr int THREADS = (LIVE + 31) / 32 * 32;
     static constexpr int S = LPR >= 32 ? LPR / 32 : 1;  // warps per row
-    static constexpr int PD = SHL_ROWS_PD;         // planes copied ahead of use
+    static constexpr int PD = rows_pd_of(R);       // planes copied ahead of use
     static constexpr int NSLOT = PD + 1;           // ring slots
     static constexpr int NODE_BYTES = 3 * NYR * R * 4;
     template <bool SMOOTH>
@@ -240,10 +252,17 @@ __device__ __forceinline__ float2 pair_modulus(const unsigned char *den_row, int
     }
 }
 
+// Work split.  The units are (load case, row tile, node plane) triples of the
+// computed load cases, ordered by case, then tile, then z; CTA b takes the
+// b-th of gridDim.x near-equal contiguous ranges.  A range cuts into z
+// segments of row-tile columns, each one z march (two halo planes), so the
+// grid balances over the SMs whatever the number of columns, and load cases
+// that have converged take no CTAs.  With as many CTAs as a multiple of the
+// columns, every range is one column chunk.
 // DOT: the fused reduction, fixed per instantiation (a.dot must match): 0
 // none, 1 p.q (q.q, mode 2, is left to the tile kernel, which serves the
-// residual applies that use it).  Launched with exactly RowShape<R>::THREADS
-// threads.
+// residual applies that use it); a CTA writes one row of six per-case sums.
+// Launched on a 1-D grid with exactly RowShape<R>::THREADS threads.
 template <int R, bool SMOOTH, int DOT>
 __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     apply_rows_kernel(const ApplyArgs<float> a, const RowConsts kc) {
@@ -251,6 +270,7 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     pdl_enter();
     using Sh = RowShape<R>;
     constexpr int TY = Sh::TY, P = Sh::P, NR = Sh::NR, NYR = Sh::NYR, S = Sh::S, PD = Sh::PD, NSLOT = Sh::NSLOT;
+    constexpr int GY = (R + TY - 1) / TY;  // row tiles per load case
     constexpr int SLOT = Sh::template slot_bytes<SMOOTH>();
     constexpr int DEN_ROW = R * (SMOOTH ? 8 : 1);
     extern __shared__ __align__(16) unsigned char rows_smem[];  // 16-byte aligned: bulk-copy destinations
@@ -258,47 +278,81 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     float *ytop = reinterpret_cast<float *>(smraw + (size_t)NSLOT * SLOT);  // [2][NR][3][R]
     float *spill = ytop + Sh::YTOP_FLOATS;                                  // [2][NR][S][2][3]
     unsigned long long *mbar = reinterpret_cast<unsigned long long *>(spill + Sh::SPILL_FLOATS);
+    __shared__ double case_sum[6];  // p.q of each load case over the CTA's segments
 
     if (a.st && a.st->nactive == 0) return;  // uniform: the solve has finished
-    const int k = blockIdx.z;
-    bool act = k < a.nvec;
-    if (act && a.st) act = a.st->active[k] != 0;
-    if (act && a.active_in) act = a.active_in[k] != 0;
-    act = act && ((a.case_mask >> k) & 1);
-    // packed compensated sum of this thread's p.q (or q.q)
-    float2 ds = make_float2(0.f, 0.f), dc = make_float2(0.f, 0.f);
-
-    if (act) {
-        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-        constexpr int LPR = Sh::LPR;
-        // every thread holds a pair when the rows fill the CTA exactly (no padding)
-        constexpr bool kFull = Sh::LIVE == Sh::THREADS && LPR == P;
-        const bool slot_ok = kFull || tid < Sh::LIVE;
-        const int jl = slot_ok ? tid % LPR : 0;  // lane within the row's lane group
-        const bool live = kFull || (slot_ok && jl < P);  // holds an element pair (padding lanes write nothing)
-        const int i = slot_ok ? tid / LPR : NR - 1;  // element row (idle threads shadow the last row)
-        const int jp = live ? jl : P - 1;        // element pair (padding lanes shadow the last pair)
-        const int x = 2 * jp;
-        const int xn = x + 2 == R ? 0 : x + 2;   // node x + 2, periodic
-        const int seg = jl / 32;
-        const size_t N = (size_t)R * R * R;
-        const int y0 = blockIdx.x * TY;
-        const int z0 = (int)(blockIdx.y * R) / a.zc, tz = (int)((blockIdx.y + 1) * R) / a.zc - z0;
-        const float *pk = a.p + (size_t)(3 * k) * N;
-        const unsigned char *den = SMOOTH ? reinterpret_cast<const unsigned char *>(a.rho) : a.mask;
-        const unsigned smem0 = smem_u32(smraw);
-        const unsigned bar0 = smem_u32(mbar);
-
-        if (tid == 0) {
-            for (int b = 0; b < NSLOT; ++b) mbar_init(bar0 + 8 * b, 1);
-            fence_barrier_init();
+    // the load cases computed (bit k), the same in every CTA (flags loaded together)
+    unsigned act = (unsigned)a.case_mask & ((1u << min(a.nvec, 6)) - 1u);
+    {
+        int fs[6], fi[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            fs[k] = a.st ? a.st->active[k] : 1;
+            fi[k] = a.active_in ? a.active_in[k] : 1;
         }
-        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (fs[k] == 0 || fi[k] == 0) act &= ~(1u << k);
+    }
+    // this CTA's range of (case, row tile, node plane) units: W / gridDim.x
+    // each, the first W % gridDim.x ranges one longer
+    static_assert(6LL * GY * R < (1LL << 31), "row apply: unit count fits 32 bits");
+    const unsigned W = (unsigned)__popc(act) * GY * R;
+    const unsigned wq = W / gridDim.x, wr = W % gridDim.x;
+    const unsigned w0 = blockIdx.x * wq + min(blockIdx.x, wr), w1 = w0 + wq + (blockIdx.x < wr ? 1u : 0u);
 
-        // plane t of the chunk = node plane z0 - 1 + t (and its element plane's density rows)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int LPR = Sh::LPR;
+    // every thread holds a pair when the rows fill the CTA exactly (no padding)
+    constexpr bool kFull = Sh::LIVE == Sh::THREADS && LPR == P;
+    const bool slot_ok = kFull || tid < Sh::LIVE;
+    const int jl = slot_ok ? tid % LPR : 0;          // lane within the row's lane group
+    const bool live = kFull || (slot_ok && jl < P);  // holds an element pair (padding lanes write nothing)
+    const int i = slot_ok ? tid / LPR : NR - 1;      // element row (idle threads shadow the last row)
+    const int jp = live ? jl : P - 1;                // element pair (padding lanes shadow the last pair)
+    const int x = 2 * jp;
+    const int xn = x + 2 == R ? 0 : x + 2;  // node x + 2, periodic
+    const int seg = jl / 32;
+    // the left neighbour pair's lane (the row is periodic: pair 0's is pair P - 1);
+    // across warps (S > 1) lane 0 takes it from the previous warp's spill word
+    const int src_lane = S > 1 ? ((lane + 31) & 31) : ((lane & ~(LPR - 1)) + (jl == 0 ? P - 1 : jl - 1));
+    const bool patch = (S > 1) && live && (lane == 0);
+    const int last_lane = S > 1 ? min(31, P - 1 - 32 * seg) : 31;  // this warp's last pair
+    const int segm1 = (seg + S - 1) % S;
+    const size_t N = (size_t)R * R * R;
+    const unsigned char *den = SMOOTH ? reinterpret_cast<const unsigned char *>(a.rho) : a.mask;
+    const unsigned smem0 = smem_u32(smraw);
+    const unsigned bar0 = smem_u32(mbar);
+
+    if (tid == 0) {
+        for (int b = 0; b < NSLOT; ++b) mbar_init(bar0 + 8 * b, 1);
+        fence_barrier_init();
+    }
+    if (DOT != 0 && tid < 6) case_sum[tid] = 0.0;
+    __syncthreads();
+
+    // packed compensated sum of this thread's p.q over the current segment
+    float2 ds = make_float2(0.f, 0.f), dc = make_float2(0.f, 0.f);
+    bool wait_ok = true;
+    unsigned g0 = 0;  // planes copied by earlier segments: plane t of this one uses ring position g0 + t
+
+    for (unsigned w = w0; w < w1;) {
+        // segment: node planes z0 .. z0 + tz - 1 of one row-tile column
+        const int col = (int)(w / R), z0 = (int)(w % R);
+        const int tz = (int)min((unsigned)(R - z0), w1 - w);
+        int k;  // the (col / GY)-th computed load case
+        {
+            unsigned m = act;
+            for (int j = col / GY; j > 0; --j) m &= m - 1;
+            k = __ffs(m) - 1;
+        }
+        const int y0 = (col % GY) * TY;
+        const float *pk = a.p + (size_t)(3 * k) * N;
+
+        // plane t of the segment = node plane z0 - 1 + t (and its element plane's density rows)
         auto issue = [&](int t) {
             if (t > tz + 1) return;
-            const int slot = t % NSLOT;
+            const int slot = (g0 + t) % NSLOT;
             const unsigned bar = bar0 + 8 * slot;
             const unsigned dst0 = smem0 + slot * SLOT;
             const int zt = wrapi(z0 - 1 + t, R);
@@ -330,15 +384,14 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
                 }
             }
         };
-        bool wait_ok = true;
         auto wait_plane = [&](int t) {
-            const int slot = t % NSLOT;
-            if (!mbar_wait_bounded(bar0 + 8 * slot, (unsigned)((t / NSLOT) & 1))) wait_ok = false;
+            const unsigned gt = g0 + t;
+            if (!mbar_wait_bounded(bar0 + 8 * (gt % NSLOT), (gt / NSLOT) & 1)) wait_ok = false;
         };
 
         // top face of plane t: Walsh-Hadamard over x, y of both elements' faces
         auto face = [&](int t, float2 (&ft)[3][4]) {
-            const float *sb = reinterpret_cast<const float *>(smraw + (t % NSLOT) * SLOT);
+            const float *sb = reinterpret_cast<const float *>(smraw + ((g0 + t) % NSLOT) * SLOT);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float *rb = sb + (c * NYR + i) * R;
@@ -369,14 +422,6 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
         wait_plane(0);
         face(0, ftb);
 
-        // the left neighbour pair's lane (the row is periodic: pair 0's is pair P - 1);
-        // across warps (S > 1) lane 0 takes it from the previous warp's spill word
-        const int src_lane = S > 1 ? ((lane + 31) & 31)
-                                   : ((lane & ~(LPR - 1)) + (jl == 0 ? P - 1 : jl - 1));
-        const bool patch = (S > 1) && live && (lane == 0);
-        const int last_lane = S > 1 ? min(31, P - 1 - 32 * seg) : 31;  // this warp's last pair
-        const int segm1 = (seg + S - 1) % S;
-
         // unrolled by two: the face arrays alternate roles between the copies
         // instead of being copied every plane
         constexpr int ZU = SHL_ROWS_ZUNROLL;
@@ -384,8 +429,8 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
         for (int s = 0; s <= tz; ++s) {
             wait_plane(s + 1);
             // moduli of element plane z0 - 1 + s (density rows of plane s)
-            const float2 Ee = pair_modulus<SMOOTH>(smraw + (s % NSLOT) * SLOT + Sh::NODE_BYTES + i * DEN_ROW, x,
-                                                   a.E, a.Evoid);
+            const float2 Ee = pair_modulus<SMOOTH>(smraw + ((g0 + s) % NSLOT) * SLOT + Sh::NODE_BYTES + i * DEN_ROW,
+                                                   x, a.E, a.Evoid);
             float2 ftt[3][4];
             face(s + 1, ftt);
             // transformed element displacements u[c][m] (mode m = x + 2y + 4z bits)
@@ -497,7 +542,7 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
                 float *qrow = a.q + (size_t)(3 * k) * N + nrow;
                 const bool pin_here = a.pin && ez == 0 && ny == 0 && x == 0;
                 // p at the pair's own nodes (x, x + 1) of node row i, bottom plane s (for p.q)
-                const float *own = reinterpret_cast<const float *>(smraw + (s % NSLOT) * SLOT) + i * R + x;
+                const float *own = reinterpret_cast<const float *>(smraw + ((g0 + s) % NSLOT) * SLOT) + i * R + x;
                 float2 v = make_float2(0.f, 0.f);  // this plane's three products (per element of the pair)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -527,24 +572,30 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) ftb[c][j] = ftt[c][j];
         }
-        if (!wait_ok && a.err) atomicOr(a.err, kApplyErrWaitTimeout);
         // every plane issued was waited for in the loop; nothing is in flight
+        g0 += tz + 2;
+        if constexpr (DOT != 0) {  // the segment's p.q into its load case's sum
+            const float2 v[1] = {df_add(two_sum(ds.x, -dc.x), two_sum(ds.y, -dc.y))};
+            double sum[1];
+            block_sum_df<1>(v, sum);
+            if (tid == 0) case_sum[k] += sum[0];
+            ds = dc = make_float2(0.f, 0.f);
+        }
+        __syncthreads();  // ring slots and +y rows are free for the next segment
+        w += tz;
     }
+    if (!wait_ok && a.err) atomicOr(a.err, kApplyErrWaitTimeout);
 
-    if constexpr (DOT == 0) return;
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    // this thread's two compensated halves as one double-float, then the CTA's
-    // row: its own case's sum in column k, zeros elsewhere
-    const float2 v[1] = {df_add(two_sum(ds.x, -dc.x), two_sum(ds.y, -dc.y))};
-    double sum[1];
-    block_sum_df<1>(v, sum);
-    if (threadIdx.x < 6) a.partial[(size_t)bid * 6 + threadIdx.x] = threadIdx.x == (unsigned)k ? sum[0] : 0.0;
-    if (a.defer) return;  // the consumer reduces the per-CTA partials itself
-    if (!last_block_ticket(a.ticket, nblocks)) return;
-    __shared__ double tot[6];
-    sum_partials_ordered<6>(a.partial, nblocks, tot);
-    if (threadIdx.x == 0) apply_dot_finish(a, tot);
+    if constexpr (DOT != 0) {
+        // the CTA's row of partials: one sum per load case (zero where it had no segment)
+        const unsigned nblocks = gridDim.x;
+        if (tid < 6) a.partial[(size_t)blockIdx.x * 6 + tid] = case_sum[tid];
+        if (a.defer) return;  // the consumer reduces the per-CTA partials itself
+        if (!last_block_ticket(a.ticket, nblocks)) return;
+        __shared__ double tot[6];
+        sum_partials_ordered<6>(a.partial, nblocks, tot);
+        if (tid == 0) apply_dot_finish(a, tot);
+    }
 }
 
 }  // namespace shl

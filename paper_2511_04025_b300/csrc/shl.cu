@@ -154,22 +154,29 @@ inline int rows_occupancy(int r, bool smooth) {
     }
     return -1;
 }
-// z chunks of the row apply: the same makespan model as pick_zc over
-// r / TY row tiles per load case.
-inline int pick_zc_rows(int r, int nvec, int ctas_per_sm) {
-    const long long nxy = (long long)((r + rows_ty(r) - 1) / rows_ty(r)) * nvec;
+// CTAs of the row apply (a 1-D grid over contiguous ranges of (case, row
+// tile, node plane) units; see apply_rows_kernel).  Two candidates by their
+// makespan in planes per CTA (each z segment adds two halo planes): a
+// multiple of the row-tile columns, every CTA one equal z chunk of one column
+// (balanced when the columns divide the resident CTAs well), or every
+// resident CTA with ranges that straddle column ends.
+inline int rows_ctas(int r, int nvec, int ctas_per_sm) {
+    const long long ncol = (long long)((r + rows_ty(r) - 1) / rows_ty(r)) * nvec;
     const long long slots = 148LL * ctas_per_sm;
-    int best = 1;
-    long long best_cost = -1;
-    for (int zc = 1; zc <= r && zc <= 128; ++zc) {
-        const long long h = (r + zc - 1) / zc;
-        const long long cost = ((nxy * zc + slots - 1) / slots) * (h + 2);
-        if (best_cost < 0 || cost < best_cost) {
-            best = zc;
-            best_cost = cost;
-        }
+    const long long W = ncol * r;
+    long long best_nb = 0, best_cost = -1;
+    if (ncol <= slots) {
+        const long long m = std::min<long long>(slots / ncol, r);
+        best_nb = ncol * m;
+        best_cost = (r + m - 1) / m + 2;
     }
-    return best;
+    {
+        const long long nb = std::max(1LL, std::min(slots, W / 4));
+        const long long L = (W + nb - 1) / nb;
+        const long long cost = L + 2 * (1 + (L - 1 + r - 1) / r);
+        if (best_cost < 0 || cost < best_cost) best_nb = nb;
+    }
+    return (int)best_nb;
 }
 
 // Launch geometry of the apply for grid r, nvec load cases and a density
@@ -178,13 +185,16 @@ inline int pick_zc_rows(int r, int nvec, int ctas_per_sm) {
 // deferred p.q partials are laid out by it (gx * gy rows per load case).
 struct ApplyGeom {
     int gx, gy, rows;
+    // rows of per-CTA p.q partials: one per CTA of the 1-D row-apply grid, one
+    // per CTA and load case of the tile kernel's (gx, gy, nvec) grid
+    size_t partial_rows(int nvec) const { return rows ? (size_t)gx : (size_t)gx * gy * nvec; }
 };
 template <typename T>
 inline ApplyGeom apply_geom(int r, int nvec, const uint8_t *mask, const double *rho) {
     const void *den = rho ? (const void *)rho : (const void *)mask;
     if (std::is_same<T, float>::value && rows_grid(r) && den && (reinterpret_cast<uintptr_t>(den) & 15) == 0) {
         const int occ = rows_occupancy(r, rho != nullptr);
-        if (occ > 0) return ApplyGeom{(r + rows_ty(r) - 1) / rows_ty(r), pick_zc_rows(r, nvec, occ), 1};
+        if (occ > 0) return ApplyGeom{rows_ctas(r, nvec, occ), 1, 1};
     }
     return ApplyGeom{((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY), apply_zc<T>(r, nvec), 0};
 }
@@ -222,8 +232,8 @@ inline int launch_apply_rows(shl_ctx *ctx, ApplyArgs<T> a, const ApplyGeom &geo,
         }
         if (!(dev < 1e-5)) return set_err(ctx, SHL_EINVAL, "element blocks off their closed form (%g)", dev);
         if (!a.err) SHL_TRY(ws_get_t(ctx, "apply_err", 1, &a.err));
-        a.zc = geo.gy;
-        const dim3 g(geo.gx, geo.gy, a.nvec);
+        a.zc = 1;
+        const dim3 g(geo.gx, 1, 1);
         switch (a.r) {
             case 32: rows_launch_r<32>(g, s, a, kc); break;
             case 48: rows_launch_r<48>(g, s, a, kc); break;
@@ -254,7 +264,7 @@ int launch_apply(shl_ctx *ctx, ApplyArgs<T> a, cudaStream_t s) {
             if (a.dot) {
                 if (!a.partial) {
                     double *partial = nullptr;
-                    SHL_TRY(ws_get_t(ctx, "apply_partial", (size_t)geo.gx * geo.gy * a.nvec * 6, &partial));
+                    SHL_TRY(ws_get_t(ctx, "apply_partial", geo.partial_rows(a.nvec) * 6, &partial));
                     a.partial = partial;
                 }
                 if (!a.ticket) {
@@ -646,11 +656,10 @@ inline int active_chunk_list(shl_ctx *ctx, int r, const Density &den, VecGeom *g
     return SHL_OK;
 }
 
-// Apply grid CTAs per load case (the deferred p.q partials of one case).
+// Rows of deferred p.q partials the six-case apply writes.
 template <typename T>
-inline int apply_ctas_per_case(int r, const Density &den) {
-    const ApplyGeom g = apply_geom<T>(r, 6, den.mask, den.rho);
-    return g.gx * g.gy;
+inline int apply_partial_rows(int r, const Density &den) {
+    return (int)apply_geom<T>(r, 6, den.mask, den.rho).partial_rows(6);
 }
 
 template <typename T>
@@ -693,7 +702,7 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     a.ticket = &st->ticket_apply;
     const int chunk = 32;
     {
-        const size_t nblk = (size_t)apply_ctas_per_case<T>(r, den) * 6;
+        const size_t nblk = (size_t)apply_partial_rows<T>(r, den);
         double *ap = nullptr;
         SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
         a.partial = ap;
@@ -702,7 +711,7 @@ int pcg_run(shl_ctx *ctx, int r, const Density &den, const ElemOp<T> &op, Bufs<T
     IterGraph graph;
     SHL_TRY(capture_iteration(ctx, s, &graph, [&]() -> int {
         SHL_TRY(launch_apply<T>(ctx, a, s));
-        launch_vec_update<T>(ctx, va, vg, FineJacobi{}, false, ApplyDot{a.partial, apply_ctas_per_case<T>(r, den)},
+        launch_vec_update<T>(ctx, va, vg, FineJacobi{}, false, ApplyDot{a.partial, apply_partial_rows<T>(r, den)},
                              s);
         launch_vec_direction<T>(ctx, va, vg, s);
         return SHL_OK;
@@ -1290,7 +1299,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             const int chunk = use_mg ? 8 : 32;
             // workspaces the iteration uses must exist before capture
             {
-                const size_t nblk = (size_t)apply_ctas_per_case<float>(r, den) * 6;
+                const size_t nblk = (size_t)apply_partial_rows<float>(r, den);
                 double *ap = nullptr;
                 SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
                 a.partial = ap;
@@ -1304,7 +1313,7 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             if (use_mg) fj = FineJacobi{mg.lv[0].Dinv, mg.lv[0].omega, z32};
             auto iteration = [&]() -> int {
                 SHL_TRY(launch_apply<float>(ctx, a, s));
-                launch_vec_update<float>(ctx, va, vg, fj, use_mg, ApplyDot{a.partial, apply_ctas_per_case<float>(r, den)},
+                launch_vec_update<float>(ctx, va, vg, fj, use_mg, ApplyDot{a.partial, apply_partial_rows<float>(r, den)},
                                          s);
                 if (use_mg) {
                     SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, st, s, kVcFirstFused | kVcLastExternal));

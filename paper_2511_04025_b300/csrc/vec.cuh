@@ -226,8 +226,8 @@ __device__ __forceinline__ double pick6(const double (&v)[NV], int off, int k) {
 // Per-CTA partial sums of p.q left by the stiffness apply (deferred mode):
 // partial[(k * per_case + b) * 6 + k] for the per_case CTAs of load case k.
 struct ApplyDot {
-    const double *partial;
-    int per_case;
+    const double *partial;  // [rows][6]: a CTA's sum of each load case (zero for cases it did not touch)
+    int rows;
 };
 
 // (p.q)_k of all six load cases at once, warp 0 only (one pass over the
@@ -236,9 +236,9 @@ __device__ inline void case_pq_warp(const ApplyDot &ad, double (&pq)[6]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 6; ++k) pq[k] = 0.0;
-    for (int b = lane; b < ad.per_case; b += 32)
+    for (int b = lane; b < ad.rows; b += 32)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) pq[k] += __ldcg(ad.partial + ((size_t)k * ad.per_case + b) * 6 + k);
+        for (int k = 0; k < 6; ++k) pq[k] += __ldcg(ad.partial + (size_t)b * 6 + k);
 #pragma unroll
     for (int k = 0; k < 6; ++k)
 #pragma unroll
