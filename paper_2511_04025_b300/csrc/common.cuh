@@ -58,6 +58,12 @@ struct shl_ctx {
     // instantiated PCG-iteration graphs by solve shape, refreshed per solve with
     // cudaGraphExecUpdate (an instantiation costs far more than an update)
     std::map<std::string, cudaGraphExec_t> graphs;
+    // side streams for independent setup chains (the per-level power
+    // iterations of the multigrid setup), forked from and joined back into
+    // the calling stream by events; created on first use
+    static constexpr int kAux = 4;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t aux_ev[kAux + 1] = {};
 };
 
 namespace shl {
@@ -154,6 +160,31 @@ inline void ws_free_all(shl_ctx *ctx) {
 }
 
 inline cudaStream_t pick_stream(shl_ctx *ctx, void *s) { return s ? static_cast<cudaStream_t>(s) : ctx->stream; }
+
+// The context's side streams and their fork/join events (created once).
+inline int aux_streams(shl_ctx *ctx) {
+    if (ctx->aux[0]) return SHL_OK;
+    for (int i = 0; i < shl_ctx::kAux; ++i)
+        SHL_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= shl_ctx::kAux; ++i)
+        SHL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aux_ev[i], cudaEventDisableTiming));
+    return SHL_OK;
+}
+
+// Releases the side streams (after the context's work has finished).
+inline void aux_release(shl_ctx *ctx) {
+    for (int i = 0; i < shl_ctx::kAux; ++i)
+        if (ctx->aux[i]) {
+            cudaStreamSynchronize(ctx->aux[i]);
+            cudaStreamDestroy(ctx->aux[i]);
+            ctx->aux[i] = nullptr;
+        }
+    for (int i = 0; i <= shl_ctx::kAux; ++i)
+        if (ctx->aux_ev[i]) {
+            cudaEventDestroy(ctx->aux_ev[i]);
+            ctx->aux_ev[i] = nullptr;
+        }
+}
 
 __host__ __device__ inline int wrapi(int v, int r) {
     v %= r;

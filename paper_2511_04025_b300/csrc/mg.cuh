@@ -113,16 +113,24 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
     }
 }
 
-// Level l+1 stencil from level l (Galerkin with trilinear P).  Thread = (I, delta).
+// Level l+1 stencil from level l (Galerkin with trilinear P):
+//   Sc(I, delta) = sum_a sum_b w(a) w(a + b - 2 delta) Sf(2I + a, b).
+// Thread = (I, delta, entry m): the coarse levels are small, so the nine
+// entries of a block go to nine threads (each sums its entry over (a, b) in
+// the same order as a thread per block would: the rounding of these sums
+// decides whether a mode held only by the ersatz void stays resolvable on
+// the coarsest level, so it is kept fixed).
 __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc) {
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27; t += (size_t)gridDim.x * blockDim.x) {
-        const size_t I = t / 27;
-        const int dl = (int)(t % 27);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27 * 9; t += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(t % 9);
+        const size_t Id = t / 9;
+        const size_t I = Id / 27;
+        const int dl = (int)(Id % 27);
         const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
         const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
-        float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        float acc = 0.0f;
         for (int az = -1; az <= 1; ++az)
             for (int ay = -1; ay <= 1; ++ay)
                 for (int ax = -1; ax <= 1; ++ax) {
@@ -134,14 +142,11 @@ __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, 
                             for (int bx = -1; bx <= 1; ++bx) {
                                 const float wb = tri_w(ax + bx - 2 * dx, ay + by - 2 * dy, az + bz - 2 * dz);
                                 if (wb == 0.0f) continue;
-                                const float w = wa * wb;
                                 const int bl = (bz + 1) * 9 + (by + 1) * 3 + (bx + 1);
-#pragma unroll
-                                for (int m = 0; m < 9; ++m) acc[m] += w * Sf[(fi * 27 + bl) * 9 + m];
+                                acc += (wa * wb) * __ldg(Sf + (fi * 27 + bl) * 9 + m);
                             }
                 }
-#pragma unroll
-        for (int m = 0; m < 9; ++m) Sc[(I * 27 + dl) * 9 + m] = acc[m];
+        Sc[Id * 9 + m] = acc;
     }
 }
 

@@ -242,6 +242,7 @@ inline void serve_stop(shl_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto *w : sv->slot_ctx) {
         cudaStreamSynchronize(w->stream);
+        aux_release(w);
         ws_free_all(w);
         cudaStreamDestroy(w->stream);
         delete w;

@@ -896,7 +896,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     ++ctx->launches;
     for (int l = 1; l <= mg->L; ++l) {
         MgLevel &L = mg->lv[l];
-        const int g = grid1d(L.N * 27, kBlk, 148 * 16);
+        const int g = grid1d(L.N * 27 * (l == 1 ? 1 : 9), kBlk, 148 * 16);  // coarse-from-coarse: a thread per entry
         if (l == 1)
             mg_galerkin_fine_kernel<<<g, kBlk, 0, s>>>(L.r, den.mask, den.rho, (float)den.E, (float)den.Ev,
                                                        (float)(1.0 / r), childM, L.S);
@@ -934,18 +934,37 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         unsigned *ptick = nullptr;
         float *py = nullptr;
         PcgState *pst = nullptr;
+        // per level: its own scratch vector, partials and ticket, so that the
+        // levels' chains (each a serial run of small, latency-bound launches)
+        // run side by side on the context's side streams
+        constexpr size_t kPowPart = 148 * 8;
+        size_t ny = 0;
+        for (int l = 0; l < mg->L; ++l) ny += 3 * mg->lv[l].N;
         SHL_TRY(ws_get_t(ctx, "mg_pow", (size_t)kMgMaxLevels * kPow, &pw));
-        SHL_TRY(ws_get_t(ctx, "mg_pow_partial", (size_t)148 * 8, &ppart));
-        SHL_TRY(ws_get_t(ctx, "mg_pow_ticket", 1, &ptick));
-        SHL_TRY(ws_get_t(ctx, "mg_pow_y", 3 * mg->lv[0].N, &py));
+        SHL_TRY(ws_get_t(ctx, "mg_pow_partial", kPowPart * kMgMaxLevels, &ppart));
+        SHL_TRY(ws_get_t(ctx, "mg_pow_ticket", (size_t)kMgMaxLevels, &ptick));
+        SHL_TRY(ws_get_t(ctx, "mg_pow_y", ny, &py));
         SHL_TRY(ws_get_t(ctx, "mg_pow_state", 1, &pst));
+        float *x0 = nullptr;
+        SHL_TRY(ws_get_t(ctx, "z32", 18 * mg->lv[0].N, &x0));
+        unsigned *apply_err = nullptr;  // the fine apply's error word exists before the capture
+        SHL_TRY(ws_get_t(ctx, "apply_err", 1, &apply_err));
+        SHL_TRY(aux_streams(ctx));
+        // every level's chain, captured once per grid and density kind (the
+        // launches are host-bound: hundreds of short kernels) and replayed
+        auto power = [&]() -> int {
         mg_power_state_kernel<<<1, 32, 0, s>>>(pst);
         ++ctx->launches;
+        SHL_CUDA(ctx, cudaEventRecord(ctx->aux_ev[shl_ctx::kAux], s));
+        size_t yo = 0;
         for (int l = 0; l < mg->L; ++l) {
             MgLevel &L = mg->lv[l];
-            float *x = l == 0 ? nullptr : L.x;
-            if (l == 0) SHL_TRY(ws_get_t(ctx, "z32", 18 * L.N, &x));
-            mg_power_seed_kernel<<<grid1d(3 * L.N), kBlk, 0, s>>>(L.N, x);
+            const cudaStream_t sl = ctx->aux[l % shl_ctx::kAux];
+            if (l < shl_ctx::kAux) SHL_CUDA(ctx, cudaStreamWaitEvent(sl, ctx->aux_ev[shl_ctx::kAux], 0));
+            float *x = l == 0 ? x0 : L.x;
+            float *yl = py + yo;
+            yo += 3 * L.N;
+            mg_power_seed_kernel<<<grid1d(3 * L.N), kBlk, 0, sl>>>(L.N, x);
             ++ctx->launches;
             for (int it = 0; it < kPow; ++it) {
                 if (l == 0) {
@@ -954,17 +973,28 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
                     a.p = x;
                     a.q = L.t;
                     a.pin = 1;
-                    SHL_TRY(launch_apply<float>(ctx, a, s));
+                    a.err = apply_err;
+                    SHL_TRY(launch_apply<float>(ctx, a, sl));
                 } else {
-                    launch_stencil(L, x, nullptr, 1.0f, 0, L.t, pst, s);
+                    launch_stencil(L, x, nullptr, 1.0f, 0, L.t, pst, sl);
                     ++ctx->launches;
                 }
-                const int g = grid1d(L.N, kBlk, 148 * 8);
-                mg_power_dinv_kernel<<<g, kBlk, 0, s>>>(L.N, L.t, L.Dinv, py, ppart, ptick, pw + l * kPow + it);
-                mg_power_scale_kernel<<<grid1d(3 * L.N), kBlk, 0, s>>>(L.N, py, pw + l * kPow + it, x);
+                const int g = grid1d(L.N, kBlk, (int)kPowPart);
+                mg_power_dinv_kernel<<<g, kBlk, 0, sl>>>(L.N, L.t, L.Dinv, yl, ppart + kPowPart * l, ptick + l,
+                                                         pw + l * kPow + it);
+                mg_power_scale_kernel<<<grid1d(3 * L.N), kBlk, 0, sl>>>(L.N, yl, pw + l * kPow + it, x);
                 ctx->launches += 2;
             }
         }
+        for (int i = 0; i < std::min(mg->L, shl_ctx::kAux); ++i) {  // join
+            SHL_CUDA(ctx, cudaEventRecord(ctx->aux_ev[i], ctx->aux[i]));
+            SHL_CUDA(ctx, cudaStreamWaitEvent(s, ctx->aux_ev[i], 0));
+        }
+        return SHL_OK;
+        };
+        IterGraph pg;
+        SHL_TRY(capture_iteration(ctx, s, &pg, power, "mgpow_" + std::to_string(r) + (den.rho ? "_s" : "_m")));
+        SHL_TRY(replay(ctx, s, &pg, 1));
         SHL_CUDA(ctx, cudaMemcpyAsync(hpw, pw, (size_t)mg->L * kPow * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     // coarsest: dense, coarse node 0 pinned, factored in FP64 on the host
@@ -1759,6 +1789,7 @@ int shl_destroy(shl_ctx *ctx) {
     cudaSetDevice(ctx->device);
     serve_stop(ctx);
     cudaStreamSynchronize(ctx->stream);
+    aux_release(ctx);
     ws_free_all(ctx);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
