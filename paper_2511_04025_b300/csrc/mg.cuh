@@ -685,6 +685,19 @@ __global__ void mg_power_state_kernel(PcgState *st) {
     }
 }
 
+// State that gates a V-cycle to the load cases in mask (bit k): the reliable
+// update preconditions only the residuals it has just replaced.
+__global__ void mg_mask_state_kernel(PcgState *st, int mask) {
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int k = 0; k < 6; ++k) {
+            st->active[k] = (mask >> k) & 1;
+            na += st->active[k];
+        }
+        st->nactive = na;
+    }
+}
+
 __global__ void mg_power_scale_kernel(size_t N, const float *y, const double *nrm2, float *x) {
     const float inv = (float)(1.0 / sqrt(nrm2[0] > 0.0 ? nrm2[0] : 1.0));
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < 3 * N; n += (size_t)gridDim.x * blockDim.x)

@@ -1309,8 +1309,10 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             Mg mg;
             const bool use_mg = (o->precond == SHL_PRECOND_MG) && mg_plan(r, &mg);
             float *z32 = nullptr;
+            PcgState *vc_state = nullptr;  // gates the reliable update's V-cycle to the updated load cases
             if (use_mg) {
                 SHL_TRY(ws_get_t(ctx, "z32", NV, &z32));
+                SHL_TRY(ws_get_t(ctx, "mg_vc_state", 1, &vc_state));
                 SHL_TRY(mg_setup(ctx, r, den, o, &mg, s));
             }
             out->precond = use_mg ? SHL_PRECOND_MG : SHL_PRECOND_JACOBI;
@@ -1387,7 +1389,9 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                     reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, r64, mask, restart, rr_true);
                     ++ctx->launches;
                     if (use_mg) {  // direction restarts from the preconditioned true residual
-                        SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, nullptr, s));
+                        mg_mask_state_kernel<<<1, 32, 0, s>>>(vc_state, mask);
+                        ++ctx->launches;
+                        SHL_TRY(mg_vcycle(ctx, &mg, a, b.r, z32, vc_state, s));
                         pcg_restart_z_kernel<float><<<gv, kBlk, 0, s>>>(va, mask);
                         ++ctx->launches;
                     }
