@@ -408,31 +408,40 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__r
 
 // The same stencil, one thread per (node, load case).  A block takes 32
 // consecutive nodes and the six load cases (warp w = load case w): it first
-// copies the 32 nodes' stencils (contiguous, 31 KB) into shared memory with
-// 16-byte loads, then each thread accumulates its three output components
-// over the 27 offsets from shared memory (node stride 243 floats: lanes hit
-// distinct banks) and three coalesced loads of x per offset.  No warp
-// reduce-scatter, ~3.5x fewer instructions than one warp per node, and six
-// warps per 32 nodes of parallelism.
-constexpr int kStencilNodes = 32;
+// copies the 32 nodes' stencils (contiguous, 31 KB) into shared memory at a
+// node pitch of 244 floats, so that every node's record starts on 16 bytes,
+// then each thread accumulates its three output components over the 27
+// offsets, reading its node's blocks four offsets (36 floats, nine 16-byte
+// loads) at a time (pitch 244: the eight lanes of a 16-byte load phase hit
+// distinct bank groups), with three coalesced loads of x per offset.  The
+// sums are formed in the same order as with one block at a time.
+constexpr int kStencilNodes = 32, kStencilPitch = 244;
 __global__ void __launch_bounds__(6 * kStencilNodes) mg_stencil_nc_kernel(int r, const float *__restrict__ S,
                                                                         const float *__restrict__ x,
                                                                         const float *__restrict__ b,
                                                                         const float *__restrict__ Dinv, float w,
                                                                         int mode, float *__restrict__ out,
                                                                         const PcgState *st) {
-    __shared__ __align__(16) float sS[kStencilNodes * 243];
+    __shared__ __align__(16) float sS[kStencilNodes * kStencilPitch];
     pdl_enter();
     if (mg_done(st)) return;
     const unsigned N = (unsigned)r * r * r;
     const unsigned n0 = blockIdx.x * kStencilNodes;
     const unsigned nn = min((unsigned)kStencilNodes, N - n0);
     {
-        const unsigned cnt = nn * 243;  // n0 * 243 floats is a multiple of 4 (n0 a multiple of 32)
-        const float4 *src = reinterpret_cast<const float4 *>(S + (size_t)n0 * 243);
-        float4 *dst = reinterpret_cast<float4 *>(sS);
-        for (unsigned i = threadIdx.x; i < cnt / 4; i += blockDim.x) dst[i] = __ldg(src + i);
-        for (unsigned i = (cnt / 4) * 4 + threadIdx.x; i < cnt; i += blockDim.x) sS[i] = __ldg(S + (size_t)n0 * 243 + i);
+        // 16-byte loads (n0 * 243 floats is a multiple of 4: n0 is a multiple of 32), scattered to the pitch
+        const unsigned cnt = nn * 243;
+        const float *src = S + (size_t)n0 * 243;
+        const float4 *src4 = reinterpret_cast<const float4 *>(src);
+        for (unsigned i4 = threadIdx.x; i4 < cnt / 4; i4 += blockDim.x) {
+            const float4 v = __ldg(src4 + i4);
+            const unsigned i = 4 * i4;
+            sS[i + i / 243] = v.x;
+            sS[i + 1 + (i + 1) / 243] = v.y;
+            sS[i + 2 + (i + 2) / 243] = v.z;
+            sS[i + 3 + (i + 3) / 243] = v.w;
+        }
+        for (unsigned i = (cnt / 4) * 4 + threadIdx.x; i < cnt; i += blockDim.x) sS[i + i / 243] = __ldg(src + i);
     }
     __syncthreads();
     const int k = threadIdx.x / kStencilNodes, lane = threadIdx.x % kStencilNodes;
@@ -441,20 +450,33 @@ __global__ void __launch_bounds__(6 * kStencilNodes) mg_stencil_nc_kernel(int r,
     const unsigned n = n0 + lane;
     const int ix = (int)(n % (unsigned)r), iy = (int)((n / (unsigned)r) % (unsigned)r), iz = (int)(n / ((unsigned)r * r));
     const float *x0p = x + (size_t)(3 * k) * N, *x1p = x0p + N, *x2p = x1p + N;
-    const float *B = sS + lane * 243;
+    unsigned xo[3], yo[3], zo[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xo[d] = (unsigned)wrap_l(ix + d - 1, r);
+        yo[d] = (unsigned)wrap_l(iy + d - 1, r) * (unsigned)r;
+        zo[d] = (unsigned)wrap_l(iz + d - 1, r) * (unsigned)r * (unsigned)r;
+    }
+    const float4 *B4 = reinterpret_cast<const float4 *>(sS + lane * kStencilPitch);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-        const unsigned zz = (unsigned)wrap_l(iz + dz, r);
+    for (int g = 0; g < 7; ++g) {  // offsets 4g .. 4g + 3 (the last group has three)
+        constexpr int kMaxQ = 9;
+        float bv[4 * kMaxQ];
+        const int nq = g < 6 ? 9 : 7;
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const unsigned row = (zz * r + (unsigned)wrap_l(iy + dy, r)) * r;
+        for (int qi = 0; qi < kMaxQ; ++qi)
+            if (qi < nq) {
+                const float4 v = B4[g * 9 + qi];
+                bv[4 * qi] = v.x, bv[4 * qi + 1] = v.y, bv[4 * qi + 2] = v.z, bv[4 * qi + 3] = v.w;
+            }
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const unsigned j = row + (unsigned)wrap_l(ix + dx, r);
-                const int dl = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+        for (int o = 0; o < 4; ++o) {
+            const int dl = 4 * g + o;
+            if (dl < 27) {
+                const unsigned j = zo[dl / 9] + yo[(dl / 3) % 3] + xo[dl % 3];
                 const float v0 = __ldg(x0p + j), v1 = __ldg(x1p + j), v2 = __ldg(x2p + j);
-                const float *Bd = B + dl * 9;
+                const float *Bd = bv + o * 9;
                 a0 += Bd[0] * v0 + Bd[1] * v1 + Bd[2] * v2;
                 a1 += Bd[3] * v0 + Bd[4] * v1 + Bd[5] * v2;
                 a2 += Bd[6] * v0 + Bd[7] * v1 + Bd[8] * v2;
