@@ -307,18 +307,24 @@ __host__ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
 __host__ __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
 
 // Conversions of the 18 planes (N values each) of the load cases in `mask`.
+// (one thread per node and its 18 planes: no per-element division)
 __global__ void to_dfloat_kernel(size_t N, int mask, const double *__restrict__ x, dfloat *__restrict__ y) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 18 * N; i += (size_t)gridDim.x * blockDim.x)
-        if ((mask >> (i / N / 3)) & 1) y[i] = dfloat(x[i]);
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int pl = 0; pl < 18; ++pl)
+            if ((mask >> (pl / 3)) & 1) y[(size_t)pl * N + n] = dfloat(x[(size_t)pl * N + n]);
 }
 // in place: element i is read as a dfloat and written back as a double
 __global__ void dfloat_to_double_kernel(size_t N, int mask, double *xy) {
     const dfloat *y = reinterpret_cast<const dfloat *>(xy);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 18 * N; i += (size_t)gridDim.x * blockDim.x)
-        if ((mask >> (i / N / 3)) & 1) {
-            const dfloat v = y[i];
-            xy[i] = (double)v;
-        }
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int pl = 0; pl < 18; ++pl)
+            if ((mask >> (pl / 3)) & 1) {
+                const size_t i = (size_t)pl * N + n;
+                const dfloat v = y[i];
+                xy[i] = (double)v;
+            }
 }
 
 // Per-thread dot-product accumulator.  FP64 vectors accumulate in FP64.  FP32

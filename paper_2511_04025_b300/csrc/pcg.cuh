@@ -260,14 +260,18 @@ __global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
 // residual along the same conjugate direction.
 
 // x64 += x32 ; x32 = 0 for the load cases in mask
-__global__ void reliable_fold_kernel(size_t N, float *x32, double *x64, int mask) {
+// x64 += x32, x32 = 0 for the load cases in mask; with xdf, also the new x64
+// as double-floats (the operand of the true-residual apply that follows).
+__global__ void reliable_fold_kernel(size_t N, float *x32, double *x64, int mask, dfloat *xdf) {
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         for (int k = 0; k < 6; ++k) {
             if (!((mask >> k) & 1)) continue;
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
-                x64[o] += (double)x32[o];
+                const double v = x64[o] + (double)x32[o];
+                x64[o] = v;
                 x32[o] = 0.0f;
+                if (xdf) xdf[o] = dfloat(v);
             }
         }
     }
@@ -278,8 +282,11 @@ __global__ void reliable_fold_kernel(size_t N, float *x32, double *x64, int mask
 // FP32 residual claimed convergence); r = r_new; rz, rr for mask.
 // Last block: a load case stays active unless its true FP64 residual
 // (rr_true, squared) meets tol2 * bnorm2 or its iteration budget is spent.
-__global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, int mask, int restart,
-                                       const double *rr_true) {
+// The true residual comes as doubles (r64) or, straight from the
+// double-float apply, as double-floats (rdf; rounded to FP32 as their exact
+// sum would be).
+__global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, const dfloat *rdf, int mask,
+                                       int restart, const double *rr_true) {
     PcgState *st = a.st;
     DotAcc<float> dacc[12];
     const size_t N = a.N;
@@ -291,7 +298,7 @@ __global__ void reliable_rebase_kernel(VecArgs<float> a, const double *r64, int 
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const size_t o = (size_t)(3 * k + i) * N + n;
-                const float rn = (float)r64[o];
+                const float rn = rdf ? __fadd_rn(rdf[o].hi, rdf[o].lo) : (float)r64[o];
                 if (!a.z) {
                     if ((restart >> k) & 1)
                         a.p[o] = di * rn;

@@ -744,17 +744,21 @@ struct SolveOut {
 // the way in, the result converted back in place): ~3x faster than FP64 on
 // B300 and far more accurate than the refinement needs.  The FP64 solver
 // keeps FP64.
+// With opdf the residual is formed in double-float arithmetic: x is converted
+// first (or taken as already converted from xdf_in), and the result is left
+// as double-floats in out when out_df, else converted to doubles in place.
 inline int resid64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double> &op, const double *x, double *out,
-                   int pin, double *dot_out, cudaStream_t s, int mask = 0x3f, const ElemOp<dfloat> *opdf = nullptr) {
+                   int pin, double *dot_out, cudaStream_t s, int mask = 0x3f, const ElemOp<dfloat> *opdf = nullptr,
+                   const dfloat *xdf_in = nullptr, bool out_df = false) {
     if (opdf) {
         const size_t N = (size_t)r * r * r;
-        dfloat *xdf = nullptr;
+        dfloat *xdf = const_cast<dfloat *>(xdf_in);
         double *partial = nullptr;
-        if (x) SHL_TRY(ws_get_t(ctx, "resid_xdf", 18 * N, &xdf));
+        if (x && !xdf) SHL_TRY(ws_get_t(ctx, "resid_xdf", 18 * N, &xdf));
         const size_t rows = (size_t)((r + kTX - 1) / kTX) * ((r + kTY - 1) / kTY) * apply_zc<dfloat>(r, 6) * 6;
         SHL_TRY(ws_get_t(ctx, "resid_partial", rows * 6, &partial));
-        if (x) {  // x == null: the residual of the zero iterate (the loads)
-            to_dfloat_kernel<<<grid1d(18 * N, kBlk, 148 * 8), kBlk, 0, s>>>(N, mask, x, xdf);
+        if (x && !xdf_in) {  // x == null: the residual of the zero iterate (the loads)
+            to_dfloat_kernel<<<grid1d(N, kBlk, 148 * 8), kBlk, 0, s>>>(N, mask, x, xdf);
             ++ctx->launches;
         }
         ApplyArgs<dfloat> a = make_apply<dfloat>(r, den, *opdf);
@@ -767,8 +771,10 @@ inline int resid64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double>
         a.dot_out = dot_out;
         a.partial = partial;
         SHL_TRY(launch_apply<dfloat>(ctx, a, s));
-        dfloat_to_double_kernel<<<grid1d(18 * N, kBlk, 148 * 8), kBlk, 0, s>>>(N, mask, out);
-        ++ctx->launches;
+        if (!out_df) {
+            dfloat_to_double_kernel<<<grid1d(N, kBlk, 148 * 8), kBlk, 0, s>>>(N, mask, out);
+            ++ctx->launches;
+        }
         return SHL_OK;
     }
     ApplyArgs<double> a = make_apply<double>(r, den, op);
@@ -1308,6 +1314,8 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             // multigrid preconditioner (when the grid coarsens far enough)
             Mg mg;
             const bool use_mg = (o->precond == SHL_PRECOND_MG) && mg_plan(r, &mg);
+            dfloat *xdf = nullptr;  // x64 as double-floats, written by the fold for the true residual
+            SHL_TRY(ws_get_t(ctx, "resid_xdf", 18 * N, &xdf));
             float *z32 = nullptr;
             PcgState *vc_state = nullptr;  // gates the reliable update's V-cycle to the updated load cases
             if (use_mg) {
@@ -1383,10 +1391,12 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
                     }
                 if (mask) {
                     ++updates;
-                    reliable_fold_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, x64, mask);
+                    // fold x32 into x64 (also as double-floats), the true residual left as double-floats
+                    reliable_fold_kernel<<<grid1d(N), kBlk, 0, s>>>(N, b.x, x64, mask, xdf);
                     ++ctx->launches;
-                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, mask, opdf));
-                    reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, r64, mask, restart, rr_true);
+                    SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, norms + 12, s, mask, opdf, xdf, true));
+                    reliable_rebase_kernel<<<gv, kBlk, 0, s>>>(va, nullptr, reinterpret_cast<const dfloat *>(r64),
+                                                               mask, restart, rr_true);
                     ++ctx->launches;
                     if (use_mg) {  // direction restarts from the preconditioned true residual
                         mg_mask_state_kernel<<<1, 32, 0, s>>>(vc_state, mask);
