@@ -175,6 +175,30 @@ def dist_setup(n_gpus):
     return rank, world, local
 
 
+def max_over_ranks(world, *vals):
+    """Each value's largest over the ranks (the job takes as long as its
+    slowest replica; errors are as large as the worst one)."""
+    if world <= 1:
+        return tuple(float(v) for v in vals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return tuple(float(v) for v in t)
+
+
+def rank_seeds(rank, n):
+    """Design seeds of one replica: disjoint across ranks (rank r uses
+    100000 r + i), so the job's designs are all different."""
+    return [100000 * rank + i for i in range(n)]
+
+
+def job_rate(world, steps, per_step, seconds):
+    """Whole-job throughput: every rank did steps x per_step designs in the
+    (max-over-ranks) time."""
+    return world * steps * per_step / seconds
+
+
 def bench_config(args, r, desc, world):
     """The workload the headline line is quoted on (both arms print it)."""
     B = max(1, args.batch_designs)
@@ -786,7 +810,7 @@ def main():
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
     B = max(1, args.batch_designs)
-    designs = [getattr(inputs, gen)(100000 * rank + i) for i in range((args.warmup + args.steps) * B)]
+    designs = [getattr(inputs, gen)(sd) for sd in rank_seeds(rank, (args.warmup + args.steps) * B)]
     batches = [designs[k * B:(k + 1) * B] for k in range(args.warmup + args.steps)]
 
     def solve(batch):
@@ -827,13 +851,9 @@ def main():
     c1 = shl.shl_get_counters(h)["kernel_launches"]
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     wall_s = sum(wall)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_s, wall_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s, wall_s = float(t[0]), float(t[1])
-    value = world * args.steps * B / dev_s
-    e2e = world * args.steps * B / wall_s
+    dev_s, wall_s = max_over_ranks(world, dev_s, wall_s)
+    value = job_rate(world, args.steps, B, dev_s)
+    e2e = job_rate(world, args.steps, B, wall_s)
 
     # the same designs one at a time (single-design latency), a sample of them
     seq = None
@@ -869,11 +889,7 @@ def main():
                                       stream=stream)
     for i, Cr in zip(check, Crs):
         acc = max(acc, float(np.max(np.abs(Cs[i] - Cr) / np.maximum(np.abs(Cr), 1e-2 * np.abs(Cr).max()))))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([acc], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        acc = float(t[0])
+    (acc,) = max_over_ranks(world, acc)
     accuracy = {"chom_entry_err_max": acc, "bound": 1e-4, "designs": len(check) * world, "reference": ref_desc}
     if args.workload == "cubic128":
         accuracy["cubic_symmetry_err_max"] = max(cubic_symmetry_err(C) for C in Cs)
