@@ -354,6 +354,15 @@ typedef struct {
 } shl_peaks;
 int shl_probe_peaks(shl_ctx *ctx, shl_peaks *out);
 
+/* Failure-detection probe of the bounded device waits (no paper
+ * counterpart): one CTA waits on an mbarrier that nothing completes, for at
+ * most `polls` polls of the same bounded wait the stiffness apply uses on its
+ * copies, then records the timeout in an error word exactly as the apply does.
+ * *timed_out = 1 when the wait ended by its bound (expected), 0 otherwise.
+ * The kernel returns normally, so the context stays usable.  polls in
+ * [1, 2^20]; synchronises the context's stream.  SHL_EINVAL on bad arguments. */
+int shl_probe_wait_timeout(shl_ctx *ctx, uint32_t polls, int32_t *timed_out);
+
 /*
  * Allocation-free variant of shl_chom (the paper has no counterpart; this is
  * an interface for callers that cannot allocate device memory, e.g. code

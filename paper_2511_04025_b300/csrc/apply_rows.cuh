@@ -132,6 +132,21 @@ __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarr
 // Error bits of the row apply (ApplyArgs::err).
 constexpr unsigned kApplyErrWaitTimeout = 1u;
 
+// Failure-detection probe: one CTA waits on an mbarrier that nothing
+// completes, with at most `polls` bounded polls, and records the timeout in
+// err as the row apply does; the kernel then returns normally.
+__global__ void probe_wait_timeout_kernel(unsigned polls, unsigned *err) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(b, 0, polls);  // phase 0 never completes: no arrival, no copy
+    if (!ok && threadIdx.x == 0) atomicOr(err, kApplyErrWaitTimeout);
+}
+
 // ---------------------------------------------------------------------------
 // Shape of one CTA
 // ---------------------------------------------------------------------------

@@ -2048,6 +2048,25 @@ int shl_probe_peaks(shl_ctx *ctx, shl_peaks *out) {
     return SHL_OK;
 }
 
+int shl_probe_wait_timeout(shl_ctx *ctx, uint32_t polls, int32_t *timed_out) {
+    if (!ctx || !timed_out) return set_err(ctx, SHL_EINVAL, "NULL argument");
+    if (polls < 1 || polls > (1u << 20)) return set_err(ctx, SHL_EINVAL, "polls %u outside [1, 2^20]", polls);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    unsigned *err = nullptr;
+    SHL_TRY(ws_get_t(ctx, "probe_err", 1, &err));
+    SHL_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    probe_wait_timeout_kernel<<<1, 32, 0, s>>>(polls, err);
+    ++ctx->launches;
+    SHL_CUDA(ctx, cudaGetLastError());
+    unsigned h = 0;
+    SHL_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SHL_CUDA(ctx, cudaStreamSynchronize(s));
+    *timed_out = (h & kApplyErrWaitTimeout) ? 1 : 0;
+    return SHL_OK;
+}
+
 int shl_get_counters(shl_ctx *ctx, shl_counters *out) {
     if (!ctx || !out) return set_err(ctx, SHL_EINVAL, "NULL argument");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);

@@ -102,6 +102,7 @@ SIGNATURES = {
                                             ctypes.POINTER(shl_stats), _vp]),
     "shl_get_counters": (ctypes.c_int, [_vp, ctypes.c_void_p]),
     "shl_probe_peaks": (ctypes.c_int, [_vp, ctypes.c_void_p]),
+    "shl_probe_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
     "shl_chom_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _vp, _vp, _vp]),
     "shl_grad": (ctypes.c_int, [_vp, ctypes.POINTER(shl_design), ctypes.c_int32, ctypes.POINTER(shl_solve_opts), _dp,
@@ -421,3 +422,11 @@ def shl_probe_peaks(ctx) -> dict:
     _check(ctx, lib().shl_probe_peaks(ctx, ctypes.byref(p)))
     return dict(fp32_fma_gflops=p.fp32_fma_gflops, fp32x2_fma_gflops=p.fp32x2_fma_gflops,
                 fp64_fma_gflops=p.fp64_fma_gflops)
+
+
+def shl_probe_wait_timeout(ctx, polls: int = 4096) -> bool:
+    """True when the probe's bounded device wait ended by its bound (the
+    expected outcome: nothing completes the barrier it waits on)."""
+    out = ctypes.c_int32(-1)
+    _check(ctx, lib().shl_probe_wait_timeout(ctx, polls, ctypes.byref(out)))
+    return out.value == 1

@@ -357,3 +357,22 @@ def test_probe_peaks_are_plausible(ctx):
     assert p["fp32_fma_gflops"] > 1e3 and p["fp64_fma_gflops"] > 10.0
     assert p["fp32x2_fma_gflops"] >= 0.9 * p["fp32_fma_gflops"]
     assert p["fp64_fma_gflops"] < 0.5 * p["fp32_fma_gflops"]
+
+
+def test_bounded_device_wait_times_out_and_the_context_survives(ctx):
+    """Failure detection without a fault: a device wait on a barrier that
+    nothing completes ends by its bound and reports the timeout in the error
+    word the stiffness apply uses; the context then still runs kernels (an
+    apply that matches the assembled oracle)."""
+    assert shl.shl_probe_wait_timeout(ctx, 2048) is True
+    r = 8
+    m = _rand_mask(r, 3)
+    x = np.random.default_rng(5).standard_normal((6, r ** 3, 3))
+    y = oracle.apply(r, m.astype(np.float64), x)
+    p = torch.tensor(oracle.aos_to_soa(x), dtype=torch.float64, device=DEV)
+    q = torch.zeros_like(p)
+    shl.shl_apply(ctx, r, p, q, mask=torch.tensor(m, device=DEV))
+    torch.cuda.synchronize()
+    assert np.abs(oracle.soa_to_aos(q.cpu().numpy()) - y).max() <= 1e-12 * np.abs(y).max()
+    with pytest.raises(shl.ShlError):
+        shl.shl_probe_wait_timeout(ctx, 0)
