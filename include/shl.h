@@ -124,7 +124,10 @@ typedef struct {
  *                  coarsest level) in FP32, used in SHL_FP32_REFINE mode when r
  *                  halves down to a coarsest grid of at most 6^3 nodes;
  *                  otherwise, and in SHL_FP64 mode, point Jacobi.
- *   mg_nu          smoothing sweeps before and after the coarse correction (<= 0: 1)
+ *   mg_nu          smoothing sweeps before and after the coarse correction on
+ *                  the fine level and the first coarse level (<= 0: 1)
+ *   mg_nu_coarse   the same on the smaller levels (index >= 2, at most 1/64 of
+ *                  the fine nodes), whose sweeps are cheap (<= 0: 3)
  *   mg_omega       block-Jacobi damping as omega * lambda_max(D^-1 A) per level,
  *                  lambda_max estimated by power iteration at setup (<= 0: 1.6);
  *                  if the preconditioned CG still breaks down, the solve is
@@ -154,6 +157,7 @@ typedef struct {
     double mg_omega;
     int32_t active;
     double cull;
+    int32_t mg_nu_coarse;
 } shl_solve_opts;
 
 /* Per-result record. */

@@ -822,7 +822,8 @@ struct Mg {
     float *Y = nullptr, *YT = nullptr;  // coarsest: inverse Cholesky factor and its transpose
     float *w = nullptr;                 // coarsest: Y b, 6 x n3
     int n3 = 0;
-    int nu = 2;
+    int nu = 2;         // sweeps per leg on levels 0 and 1
+    int nu_coarse = 3;  // sweeps per leg on levels >= 2
 };
 
 // Levels: halve while even and >= 6; usable when the coarsest is small.
@@ -871,6 +872,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     float *childM = nullptr;
     SHL_TRY(mg_child_matrices(ctx, o->nu, s, &childM));
     mg->nu = o->mg_nu > 0 ? o->mg_nu : 1;
+    mg->nu_coarse = o->mg_nu_coarse > 0 ? o->mg_nu_coarse : 3;
     char nm[64];
     for (int l = 0; l <= mg->L; ++l) {
         MgLevel &L = mg->lv[l];
@@ -1170,7 +1172,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
             SHL_TRY(fine_apply(L.x, L.t));
             restrict_to(0, L.b, L.t);
         } else {
-            for (int it = 1; it < mg->nu; ++it) sweep(L, 2);
+            for (int it = 1; it < (l >= 2 ? mg->nu_coarse : mg->nu); ++it) sweep(L, 2);
             sweep(L, 1);
             restrict_to(l, L.t, nullptr);
         }
@@ -1188,7 +1190,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
         pdl_launch(mg_prolong_kernel, dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[l + 1].r,
                    mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
         ++ctx->launches;
-        for (int it = 0; it < mg->nu; ++it) {
+        for (int it = 0; it < (l >= 2 ? mg->nu_coarse : mg->nu); ++it) {
             if (l == 0) {
                 SHL_TRY(fine_apply(L.x, L.t));
                 if (it == mg->nu - 1 && (fuse & kVcLastExternal)) break;
@@ -1521,6 +1523,8 @@ inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
         return set_err(ctx, SHL_EINVAL, "unknown preconditioner %d", o->precond);
     if (!(o->mg_omega <= 0.0 || o->mg_omega < 2.0))
         return set_err(ctx, SHL_EINVAL, "mg_omega (damping times lambda_max) must be < 2");
+    if (o->mg_nu > 64 || o->mg_nu_coarse > 64)
+        return set_err(ctx, SHL_EINVAL, "mg_nu %d / mg_nu_coarse %d above 64 sweeps", o->mg_nu, o->mg_nu_coarse);
     if (o->active != 0 && o->active != 1) return set_err(ctx, SHL_EINVAL, "active must be 0 or 1, got %d", o->active);
     if (o->active && !(o->cull < 1.0)) return set_err(ctx, SHL_EINVAL, "cull threshold %g must be < 1", o->cull);
     return SHL_OK;
@@ -1768,6 +1772,7 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->inner_tol = 1e-4;
     o->precond = SHL_PRECOND_MG;
     o->mg_nu = 1;
+    o->mg_nu_coarse = 3;
     o->mg_omega = 1.6;
     o->active = 0;
     o->cull = 1e-3;
