@@ -128,6 +128,9 @@ typedef struct {
  *                  the fine level and the first coarse level (<= 0: 1)
  *   mg_nu_coarse   the same on the smaller levels (index >= 2, at most 1/64 of
  *                  the fine nodes), whose sweeps are cheap (<= 0: 3)
+ *   mg_gamma       visits of each level >= 2 per visit of the level above: 1
+ *                  V-cycle, 2 W-cycle; 0 (default) W-cycle from r = 128 up,
+ *                  where those levels cost little next to the fine level
  *   mg_omega       block-Jacobi damping as omega * lambda_max(D^-1 A) per level,
  *                  lambda_max estimated by power iteration at setup (<= 0: 1.6);
  *                  if the preconditioned CG still breaks down, the solve is
@@ -158,6 +161,7 @@ typedef struct {
     int32_t active;
     double cull;
     int32_t mg_nu_coarse;
+    int32_t mg_gamma;
 } shl_solve_opts;
 
 /* Per-result record. */

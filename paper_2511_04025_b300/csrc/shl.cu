@@ -824,6 +824,7 @@ struct Mg {
     int n3 = 0;
     int nu = 2;         // sweeps per leg on levels 0 and 1
     int nu_coarse = 3;  // sweeps per leg on levels >= 2
+    int gamma = 1;      // visits of each level >= 2 per visit of the level above
 };
 
 // Levels: halve while even and >= 6; usable when the coarsest is small.
@@ -873,6 +874,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     SHL_TRY(mg_child_matrices(ctx, o->nu, s, &childM));
     mg->nu = o->mg_nu > 0 ? o->mg_nu : 1;
     mg->nu_coarse = o->mg_nu_coarse > 0 ? o->mg_nu_coarse : 3;
+    mg->gamma = o->mg_gamma > 0 ? o->mg_gamma : (r >= 128 ? 2 : 1);
     char nm[64];
     for (int l = 0; l <= mg->L; ++l) {
         MgLevel &L = mg->lv[l];
@@ -1156,49 +1158,61 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
             pdl_launch(mg_restrict_kernel, dim3(grid1d(Cl.N, kBlk, 148), 18), kBlk, 0, s, Cl.r, bf, tf, Cl.b, st);
         ++ctx->launches;
     };
-    for (int l = 0; l < mg->L; ++l) {  // down: pre-smooth, restrict the residual
-        MgLevel &L = mg->lv[l];
+    // fine level: pre-smoothing and the restriction of its residual
+    {
+        MgLevel &L = mg->lv[0];
         const int g = grid1d(L.N);
-        if (l == 0 && !(fuse & kVcFirstFused)) {
+        if (!(fuse & kVcFirstFused)) {
             pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, nullptr, L.Dinv, L.omega, L.x, 1, st);
             ++ctx->launches;
         }
-        if (l == 0) {
-            for (int it = 1; it < mg->nu; ++it) {
-                SHL_TRY(fine_apply(L.x, L.t));
-                pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
-                ++ctx->launches;
-            }
+        for (int it = 1; it < mg->nu; ++it) {
             SHL_TRY(fine_apply(L.x, L.t));
-            restrict_to(0, L.b, L.t);
-        } else {
-            for (int it = 1; it < (l >= 2 ? mg->nu_coarse : mg->nu); ++it) sweep(L, 2);
-            sweep(L, 1);
-            restrict_to(l, L.t, nullptr);
+            pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
+            ++ctx->launches;
         }
+        SHL_TRY(fine_apply(L.x, L.t));
+        restrict_to(0, L.b, L.t);
     }
-    {
-        MgLevel &C = mg->lv[mg->L];
-        const int g = grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4);
-        pdl_launch(mg_dense_y_kernel, g, kBlk, 0, s, mg->n3, (const float *)mg->Y, (const float *)C.b, mg->w, st);
-        pdl_launch(mg_dense_yt_kernel, g, kBlk, 0, s, mg->n3, (const float *)mg->YT, (const float *)mg->w, C.x, st);
-        ctx->launches += 2;
-    }
-    for (int l = mg->L - 1; l >= 0; --l) {  // up: prolongate the correction, post-smooth
+    // Coarse levels, recursively: level l's b is set; on the first visit its x
+    // holds the restriction's zero-start Jacobi step.  Levels >= 2 are visited
+    // gamma times per visit of the level above (V-cycle: 1, W-cycle: 2).
+    std::function<void(int, bool)> cycle = [&](int l, bool first) {
+        if (l == mg->L) {  // coarsest: x = Y^T (Y b)
+            MgLevel &C = mg->lv[mg->L];
+            const int g = grid1d((size_t)6 * mg->n3 * 32, kBlk, 148 * 4);
+            pdl_launch(mg_dense_y_kernel, g, kBlk, 0, s, mg->n3, (const float *)mg->Y, (const float *)C.b, mg->w, st);
+            pdl_launch(mg_dense_yt_kernel, g, kBlk, 0, s, mg->n3, (const float *)mg->YT, (const float *)mg->w, C.x,
+                       st);
+            ctx->launches += 2;
+            return;
+        }
         MgLevel &L = mg->lv[l];
-        const int g = grid1d(L.N);
+        const int nu = l >= 2 ? mg->nu_coarse : mg->nu;
+        for (int it = first ? 1 : 0; it < nu; ++it) sweep(L, 2);
+        sweep(L, 1);
+        restrict_to(l, L.t, nullptr);
+        const int visits = (l + 1 >= 2 && l + 1 < mg->L) ? mg->gamma : 1;
+        cycle(l + 1, true);
+        for (int v = 1; v < visits; ++v) cycle(l + 1, false);
         pdl_launch(mg_prolong_kernel, dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[l + 1].r,
-                   mg->lv[l + 1].x, L.x, l == 0 ? 1 : 0, st);
+                   mg->lv[l + 1].x, L.x, 0, st);
         ++ctx->launches;
-        for (int it = 0; it < (l >= 2 ? mg->nu_coarse : mg->nu); ++it) {
-            if (l == 0) {
-                SHL_TRY(fine_apply(L.x, L.t));
-                if (it == mg->nu - 1 && (fuse & kVcLastExternal)) break;
-                pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
-                ++ctx->launches;
-            } else {
-                sweep(L, 2);
-            }
+        for (int it = 0; it < nu; ++it) sweep(L, 2);
+    };
+    if (mg->L >= 1) cycle(1, true);
+    // fine level: prolongation of the correction and post-smoothing
+    {
+        MgLevel &L = mg->lv[0];
+        const int g = grid1d(L.N);
+        pdl_launch(mg_prolong_kernel, dim3(grid1d(mg->lv[1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[1].r,
+                   mg->lv[1].x, L.x, 1, st);
+        ++ctx->launches;
+        for (int it = 0; it < mg->nu; ++it) {
+            SHL_TRY(fine_apply(L.x, L.t));
+            if (it == mg->nu - 1 && (fuse & kVcLastExternal)) break;
+            pdl_launch(mg_jacobi_kernel, g, kBlk, 0, s, L.N, L.b, L.t, L.Dinv, L.omega, L.x, 0, st);
+            ++ctx->launches;
         }
     }
     SHL_CUDA(ctx, cudaGetLastError());
@@ -1525,6 +1539,7 @@ inline int validate_solve_opts(shl_ctx *ctx, const shl_solve_opts *o) {
         return set_err(ctx, SHL_EINVAL, "mg_omega (damping times lambda_max) must be < 2");
     if (o->mg_nu > 64 || o->mg_nu_coarse > 64)
         return set_err(ctx, SHL_EINVAL, "mg_nu %d / mg_nu_coarse %d above 64 sweeps", o->mg_nu, o->mg_nu_coarse);
+    if (o->mg_gamma < 0 || o->mg_gamma > 2) return set_err(ctx, SHL_EINVAL, "mg_gamma %d not 0, 1 or 2", o->mg_gamma);
     if (o->active != 0 && o->active != 1) return set_err(ctx, SHL_EINVAL, "active must be 0 or 1, got %d", o->active);
     if (o->active && !(o->cull < 1.0)) return set_err(ctx, SHL_EINVAL, "cull threshold %g must be < 1", o->cull);
     return SHL_OK;
@@ -1773,6 +1788,7 @@ void shl_default_solve_opts(shl_solve_opts *o) {
     o->precond = SHL_PRECOND_MG;
     o->mg_nu = 1;
     o->mg_nu_coarse = 3;
+    o->mg_gamma = 0;
     o->mg_omega = 1.6;
     o->active = 0;
     o->cull = 1e-3;

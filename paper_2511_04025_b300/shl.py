@@ -44,7 +44,7 @@ class shl_solve_opts(ctypes.Structure):
                 ("density", ctypes.c_int32), ("warm_start", ctypes.c_int32), ("kappa", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int32), ("mg_nu", ctypes.c_int32),
                 ("mg_omega", ctypes.c_double), ("active", ctypes.c_int32), ("cull", ctypes.c_double),
-                ("mg_nu_coarse", ctypes.c_int32)]
+                ("mg_nu_coarse", ctypes.c_int32), ("mg_gamma", ctypes.c_int32)]
 
 
 class shl_stats(ctypes.Structure):
