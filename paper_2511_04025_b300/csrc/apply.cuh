@@ -12,7 +12,9 @@
 // registers, and passes the other three corners of each node plane to its
 // +x / +y / +xy neighbours through a double-buffered shared exchange.  The
 // +z half of every element's output is carried in registers to the next
-// step, so no atomics are used and the result is deterministic.
+// step, so no atomics are used and the result is deterministic.  A warp
+// whose elements of a plane are all culled (E_e = 0: the active set of
+// Sec. 4.2.1) skips the element operator for that plane.
 //
 // Modes: plain apply (q = K p), residual (q = -sum_e K_e (p_e + chi^k), i.e.
 // f - K p), optional node-0 pin (q = 0 there: the pinned system), and fused
@@ -318,35 +320,52 @@ __global__ void __launch_bounds__(ApplyShape<T, TX, TY>::THREADS, sizeof(T) == 4
             T own_t[3];
             T ftt[3][4];
             T w[3][4];  // node-plane ez corner values (x, y butterflies undone)
+            // A warp whose elements of this plane are all culled (E_e = 0, the
+            // active set) adds exact zeros: it skips the element operator and
+            // only hands on the top faces carried from the plane below.
+            const bool void_warp = __all_sync(0xffffffffu, !el || zero_modulus(Ee));
             if (el) {
                 face((s + 1) & 1, ftt, own_t);
-                T u[3][8], y[3][8];
+                T F[3][4];
+                if (void_warp) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
+                    for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        u[c][j] = ftb[c][j] + ftt[c][j];
-                        u[c][j + 4] = ftb[c][j] - ftt[c][j];
+                        for (int j = 0; j < 4; ++j) {
+                            F[c][j] = carry[c][j];
+                            carry[c][j] = T(0);
+                        }
+                } else {
+                    T u[3][8], y[3][8];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            u[c][j] = ftb[c][j] + ftt[c][j];
+                            u[c][j + 4] = ftb[c][j] - ftt[c][j];
+                        }
+                    if (RESID) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            u[c][0] += ch0[c];
+                            u[c][1] += chd[c][0];
+                            u[c][2] += chd[c][1];
+                            u[c][4] += chd[c][2];
+                        }
                     }
-                if (RESID) {
+                    block_apply(a.op, u, y, Ee);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        u[c][0] += ch0[c];
-                        u[c][1] += chd[c][0];
-                        u[c][2] += chd[c][1];
-                        u[c][4] += chd[c][2];
-                    }
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            F[c][j] = carry[c][j] + (y[c][j] + y[c][j + 4]);
+                            carry[c][j] = y[c][j] - y[c][j + 4];
+                        }
                 }
-                block_apply(a.op, u, y, Ee);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    T F[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        F[j] = carry[c][j] + (y[c][j] + y[c][j + 4]);
-                        carry[c][j] = y[c][j] - y[c][j + 4];
-                    }
-                    const T t0 = F[0] + F[1], t1 = F[0] - F[1], t2 = F[2] + F[3], t3 = F[2] - F[3];
+                    const T t0 = F[c][0] + F[c][1], t1 = F[c][0] - F[c][1], t2 = F[c][2] + F[c][3],
+                            t3 = F[c][2] - F[c][3];
                     w[c][0] = t0 + t2;
                     w[c][1] = t1 + t3;
                     w[c][2] = t0 - t2;

@@ -26,6 +26,8 @@
 //    memory when a row spans several warps); padding lanes compute on a copy
 //    of the row's last pair and write nothing; the +y corner row goes to the
 //    next element row through shared memory (one barrier per plane).
+// A warp whose element pairs of a plane are all culled (E_e = 0: the active
+// set of Sec. 4.2.1) skips the element operator for that plane.
 // Deterministic, no atomics.
 //
 // Closed form of the transformed element blocks (element.cuh: G[c][i][j],
@@ -277,8 +279,10 @@ __device__ __forceinline__ float2 pair_modulus(const unsigned char *den_row, int
 // DOT: the fused reduction, fixed per instantiation (a.dot must match): 0
 // none, 1 p.q (q.q, mode 2, is left to the tile kernel, which serves the
 // residual applies that use it); a CTA writes one row of six per-case sums.
+// CULL (the culled void of the active set, a.Evoid = 0): a warp whose
+// element pairs of a plane are all culled skips the element operator.
 // Launched on a 1-D grid with exactly RowShape<R>::THREADS threads.
-template <int R, bool SMOOTH, int DOT>
+template <int R, bool SMOOTH, int DOT, bool CULL>
 __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
     apply_rows_kernel(const ApplyArgs<float> a, const RowConsts kc) {
     static_assert(DOT == 0 || DOT == 1, "row apply: DOT is 0 or 1");
@@ -448,72 +452,95 @@ __global__ void __launch_bounds__(RowShape<R>::THREADS, RowShape<R>::MINB)
                                                    x, a.E, a.Evoid);
             float2 ftt[3][4];
             face(s + 1, ftt);
-            // transformed element displacements u[c][m] (mode m = x + 2y + 4z bits)
-            float2 u[3][8];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                for (int j = 1; j < 4; ++j) u[c][j] = p2add(ftb[c][j], ftt[c][j]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) u[c][j + 4] = p2sub(ftb[c][j], ftt[c][j]);
-            }
-            // y = E G u in the closed form (the translation modes u[c][0] and
-            // y[c][0] are zero)
-            // E-scaled constants: scalar products with the parameter-bank values
-            // (no registers held for the constants)
-            const float2 eA = p2mul(Ee, p2splat(kc.amb)), eB = p2mul(Ee, p2splat(kc.b)),
-                         eP = p2mul(Ee, p2splat(kc.p)), eQ = p2mul(Ee, p2splat(kc.q)),
-                         eF = p2mul(Ee, p2splat(kc.f)), eR = p2mul(Ee, p2splat(kc.rr)),
-                         eD = p2mul(Ee, p2splat(kc.d));
-            float2 y[3][8];
-            {  // c = 0: (u01, u12, u24) -> (y01, y12, y24)
-                const float2 t0 = p2mul(eB, p2add(p2add(u[0][1], u[1][2]), u[2][4]));
-                y[0][1] = p2fma(eA, u[0][1], t0);
-                y[1][2] = p2fma(eA, u[1][2], t0);
-                y[2][4] = p2fma(eA, u[2][4], t0);
-            }
-            {  // c = 7: (u06, u15, u23)
-                const float2 t7 = p2mul(eD, p2add(p2add(u[0][6], u[1][5]), u[2][3]));
-                y[0][6] = p2fma(eD, u[0][6], t7);
-                y[1][5] = p2fma(eD, u[1][5], t7);
-                y[2][3] = p2fma(eD, u[2][3], t7);
-            }
-            // c = 1 (t = 0): (u13, u25); c = 2 (t = 1): (u03, u26); c = 4 (t = 2): (u05, u16)
-            y[1][3] = p2fma(eP, u[1][3], p2mul(eQ, u[2][5]));
-            y[2][5] = p2fma(eP, u[2][5], p2mul(eQ, u[1][3]));
-            y[0][3] = p2fma(eP, u[0][3], p2mul(eQ, u[2][6]));
-            y[2][6] = p2fma(eP, u[2][6], p2mul(eQ, u[0][3]));
-            y[0][5] = p2fma(eP, u[0][5], p2mul(eQ, u[1][6]));
-            y[1][6] = p2fma(eP, u[1][6], p2mul(eQ, u[0][5]));
-            // c = 6 (t = 0): u07 -> y07, (u14, u22) -> y14 = y22; c = 5 (t = 1): u17, (u04, u21);
-            // c = 3 (t = 2): u27, (u02, u11)
-            y[0][7] = p2mul(eR, u[0][7]);
-            y[1][4] = y[2][2] = p2mul(eF, p2add(u[1][4], u[2][2]));
-            y[1][7] = p2mul(eR, u[1][7]);
-            y[0][4] = y[2][1] = p2mul(eF, p2add(u[0][4], u[2][1]));
-            y[2][7] = p2mul(eR, u[2][7]);
-            y[0][2] = y[1][1] = p2mul(eF, p2add(u[0][2], u[1][1]));
-
-            // back to corners: z split (bottom face = node plane z0 - 1 + s,
-            // top face carried), then x, y.  W[c][b]: corner b = bx + 2 by of
-            // both elements (packed).
+            // A warp whose element pairs of this plane are all culled (E_e = 0,
+            // the active set) adds exact zeros: it skips the element operator
+            // and only hands on the top faces carried from the plane below.
+            bool void_warp = false;
+            if constexpr (CULL) void_warp = __all_sync(0xffffffffu, Ee.x == 0.f && Ee.y == 0.f);
+            // back to corners: z split (bottom face = node plane z0 - 1 + s, top
+            // face carried), then x, y.  W[c][b]: corner b = bx + 2 by of both
+            // elements (packed).
             float2 W[3][4];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float2 F[4];
-                F[0] = p2sub(y[c][4], carry[c][0]);  // carry[c][0] holds -(top of mode 0) = y_prev[c][4]
-                carry[c][0] = y[c][4];
-#pragma unroll
-                for (int j = 1; j < 4; ++j) {
-                    F[j] = p2add(carry[c][j], p2add(y[c][j], y[c][j + 4]));
-                    carry[c][j] = p2sub(y[c][j], y[c][j + 4]);
-                }
+            auto corners = [&](int c, const float2 (&F)[4]) {
                 const float2 t0 = p2add(F[0], F[1]), t1 = p2sub(F[0], F[1]), t2 = p2add(F[2], F[3]),
                              t3 = p2sub(F[2], F[3]);
                 W[c][0] = p2add(t0, t2);
                 W[c][1] = p2add(t1, t3);
                 W[c][2] = p2sub(t0, t2);
                 W[c][3] = p2sub(t1, t3);
+            };
+            if (void_warp) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float2 F[4];
+                    F[0] = make_float2(-carry[c][0].x, -carry[c][0].y);
+                    carry[c][0] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) {
+                        F[j] = carry[c][j];
+                        carry[c][j] = make_float2(0.f, 0.f);
+                    }
+                    corners(c, F);
+                }
+            } else {
+                // transformed element displacements u[c][m] (mode m = x + 2y + 4z bits)
+                float2 u[3][8];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) u[c][j] = p2add(ftb[c][j], ftt[c][j]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) u[c][j + 4] = p2sub(ftb[c][j], ftt[c][j]);
+                }
+                // y = E G u in the closed form (the translation modes u[c][0] and
+                // y[c][0] are zero)
+                // E-scaled constants: scalar products with the parameter-bank values
+                // (no registers held for the constants)
+                const float2 eA = p2mul(Ee, p2splat(kc.amb)), eB = p2mul(Ee, p2splat(kc.b)),
+                             eP = p2mul(Ee, p2splat(kc.p)), eQ = p2mul(Ee, p2splat(kc.q)),
+                             eF = p2mul(Ee, p2splat(kc.f)), eR = p2mul(Ee, p2splat(kc.rr)),
+                             eD = p2mul(Ee, p2splat(kc.d));
+                float2 y[3][8];
+                {  // c = 0: (u01, u12, u24) -> (y01, y12, y24)
+                    const float2 t0 = p2mul(eB, p2add(p2add(u[0][1], u[1][2]), u[2][4]));
+                    y[0][1] = p2fma(eA, u[0][1], t0);
+                    y[1][2] = p2fma(eA, u[1][2], t0);
+                    y[2][4] = p2fma(eA, u[2][4], t0);
+                }
+                {  // c = 7: (u06, u15, u23)
+                    const float2 t7 = p2mul(eD, p2add(p2add(u[0][6], u[1][5]), u[2][3]));
+                    y[0][6] = p2fma(eD, u[0][6], t7);
+                    y[1][5] = p2fma(eD, u[1][5], t7);
+                    y[2][3] = p2fma(eD, u[2][3], t7);
+                }
+                // c = 1 (t = 0): (u13, u25); c = 2 (t = 1): (u03, u26); c = 4 (t = 2): (u05, u16)
+                y[1][3] = p2fma(eP, u[1][3], p2mul(eQ, u[2][5]));
+                y[2][5] = p2fma(eP, u[2][5], p2mul(eQ, u[1][3]));
+                y[0][3] = p2fma(eP, u[0][3], p2mul(eQ, u[2][6]));
+                y[2][6] = p2fma(eP, u[2][6], p2mul(eQ, u[0][3]));
+                y[0][5] = p2fma(eP, u[0][5], p2mul(eQ, u[1][6]));
+                y[1][6] = p2fma(eP, u[1][6], p2mul(eQ, u[0][5]));
+                // c = 6 (t = 0): u07 -> y07, (u14, u22) -> y14 = y22; c = 5 (t = 1): u17, (u04, u21);
+                // c = 3 (t = 2): u27, (u02, u11)
+                y[0][7] = p2mul(eR, u[0][7]);
+                y[1][4] = y[2][2] = p2mul(eF, p2add(u[1][4], u[2][2]));
+                y[1][7] = p2mul(eR, u[1][7]);
+                y[0][4] = y[2][1] = p2mul(eF, p2add(u[0][4], u[2][1]));
+                y[2][7] = p2mul(eR, u[2][7]);
+                y[0][2] = y[1][1] = p2mul(eF, p2add(u[0][2], u[1][1]));
+
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float2 F[4];
+                    F[0] = p2sub(y[c][4], carry[c][0]);  // carry[c][0] holds -(top of mode 0) = y_prev[c][4]
+                    carry[c][0] = y[c][4];
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) {
+                        F[j] = p2add(carry[c][j], p2add(y[c][j], y[c][j + 4]));
+                        carry[c][j] = p2sub(y[c][j], y[c][j + 4]);
+                    }
+                    corners(c, F);
+                }
             }
             // x exchange: node x gets the +x corner of the left neighbour's second element
             float rb1[3], rb3[3];

@@ -53,9 +53,20 @@ __global__ void __launch_bounds__(kChomThreads) chom_kernel(const ChomArgs a) {
     for (int t = 0; t < 21; ++t) acc[t] = 0.0;
     const int r = a.r;
     const size_t N = a.N;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+    // warps step through 32 consecutive elements at a time (the element of
+    // each thread is the one of a plain grid-stride loop)
+    const unsigned lane = threadIdx.x & 31u;
+    for (size_t e0 = blockIdx.x * (size_t)blockDim.x + (threadIdx.x - lane); e0 < N;
+         e0 += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = e0 + lane;
+        const bool in = e < N;
+        const double Ee = !in ? 0.0 : (a.rho ? a.Evoid + a.rho[e] * (a.E - a.Evoid) : (a.mask[e] ? a.E : a.Evoid));
+        // culled elements (E_e = 0, the active set) add exact zeros to every
+        // energy sum: a warp of them skips the work (the sensitivity mode
+        // still needs every g_e)
+        if (__all_sync(0xffffffffu, Ee == 0.0 && !a.g)) continue;
+        if (!in) continue;
         const int ix = e % r, iy = (e / r) % r, iz = e / ((size_t)r * r);
-        const double Ee = a.rho ? a.Evoid + a.rho[e] * (a.E - a.Evoid) : (a.mask[e] ? a.E : a.Evoid);
         for (int k = 0; k < 6; ++k) {
             double w[3][8];
             load_element_field(a, ix, iy, iz, k, w);
@@ -110,6 +121,14 @@ __global__ void __launch_bounds__(kChomThreads) chom_kernel(const ChomArgs a) {
 // element energies as chom_kernel, from u already converted to dfloat (FP32
 // pairs, ~48 significant bits, far beyond that mode's tolerance), so the
 // per-element work runs on the FP32 pipes instead of B300's narrow FP64 pipe.
+//
+// A CTA takes 32 consecutive elements with one thread per (element, load
+// case): warp k moves load case k's total fields to the transformed basis
+// (shared memory), then applies the element blocks to its own field and
+// forms its energies with the load cases i <= k.  The per-thread state is
+// one load case instead of six, so several CTAs share an SM.  Groups of 32
+// elements that are all culled (E_e = 0, the active set) are skipped: their
+// energies are exact zeros.
 struct ChomDfArgs {
     int r;
     size_t N;
@@ -123,17 +142,24 @@ struct ChomDfArgs {
     ElemOp<dfloat> op;
 };
 
-__global__ void __launch_bounds__(kChomThreads) chom_df_kernel(const ChomDfArgs a) {
-    extern __shared__ dfloat wdf[];  // [6][24][blockDim] transformed total fields
-    dfloat acc[21];
-#pragma unroll
-    for (int t = 0; t < 21; ++t) acc[t] = dfloat(0.0f, 0.0f);
+constexpr int kChomDfElems = 32;                 // elements per CTA step (one per lane)
+constexpr int kChomDfThreads = 6 * kChomDfElems;  // warp k = load case k
+
+__global__ void __launch_bounds__(kChomDfThreads) chom_df_kernel(const ChomDfArgs a) {
+    __shared__ dfloat wsm[6][24][kChomDfElems];  // transformed total fields [case][component * 8 + mode][element]
     const int r = a.r;
     const size_t N = a.N;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
-        const int ix = e % r, iy = (e / r) % r, iz = e / ((size_t)r * r);
-        const dfloat Ee = dfloat(a.rho ? a.Evoid + a.rho[e] * (a.E - a.Evoid) : (a.mask[e] ? a.E : a.Evoid));
-        for (int k = 0; k < 6; ++k) {
+    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+    dfloat acc[6];  // energies (i, k) for i <= k
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i] = dfloat(0.0f, 0.0f);
+    for (size_t e0 = (size_t)blockIdx.x * kChomDfElems; e0 < N; e0 += (size_t)gridDim.x * kChomDfElems) {
+        const size_t e = e0 + lane;
+        const bool in = e < N;
+        const double Ed = !in ? 0.0 : (a.rho ? a.Evoid + a.rho[e] * (a.E - a.Evoid) : (a.mask[e] ? a.E : a.Evoid));
+        if (!__syncthreads_or(Ed != 0.0)) continue;  // all 32 elements culled (uniform)
+        if (in) {
+            const int ix = e % r, iy = (e / r) % r, iz = e / ((size_t)r * r);
             dfloat w[3][8];
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
@@ -147,31 +173,39 @@ __global__ void __launch_bounds__(kChomThreads) chom_df_kernel(const ChomDfArgs 
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int m = 0; m < 8; ++m)
-                    wdf[((k * 3 + i) * 8 + m) * blockDim.x + threadIdx.x] = w[i][m] + a.op.chihat[k][i][m];
+                for (int m = 0; m < 8; ++m) wsm[k][i * 8 + m][lane] = w[i][m] + a.op.chihat[k][i][m];
         }
-        int t = 0;
-        for (int j = 0; j < 6; ++j) {
-            dfloat wj[3][8], gj[3][8];
+        __syncthreads();
+        if (in) {
+            dfloat wk[3][8], gk[3][8];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int m = 0; m < 8; ++m) wj[i][m] = wdf[((j * 3 + i) * 8 + m) * blockDim.x + threadIdx.x];
-            block_apply(a.op, wj, gj, dfloat(1.0f, 0.0f));
-            for (int i = 0; i <= j; ++i) {
+                for (int m = 0; m < 8; ++m) wk[i][m] = wsm[k][i * 8 + m][lane];
+            block_apply(a.op, wk, gk, dfloat(1.0f, 0.0f));
+            const dfloat Ee = dfloat(Ed);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                if (i > k) break;  // uniform per warp
                 dfloat s = dfloat(0.0f, 0.0f);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) s += wdf[((i * 3 + c) * 8 + m) * blockDim.x + threadIdx.x] * gj[c][m];
-                acc[t] += Ee * s;
-                ++t;
+                    for (int m = 0; m < 8; ++m) s += wsm[i][c * 8 + m][lane] * gk[c][m];
+                acc[i] += Ee * s;
             }
         }
+        __syncthreads();  // wsm is refilled by the next step
     }
+    // energy (i, j), i <= j, is entry t = j (j + 1) / 2 + i of the 21
     float2 v[21];
 #pragma unroll
-    for (int t = 0; t < 21; ++t) v[t] = make_float2(acc[t].hi, acc[t].lo);
+    for (int t = 0; t < 21; ++t) v[t] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int i = 0; i <= j; ++i)
+            if (j == k) v[j * (j + 1) / 2 + i] = make_float2(acc[i].hi, acc[i].lo);
     double sum[21];
     block_sum_df<21>(v, sum);
 #pragma unroll

@@ -306,6 +306,12 @@ __host__ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
 }
 __host__ __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
 
+// An exactly zero element modulus: a culled element of the active set
+// (Sec. 4.2.1), whose stiffness contributions are exact zeros.
+__host__ __device__ __forceinline__ bool zero_modulus(float v) { return v == 0.0f; }
+__host__ __device__ __forceinline__ bool zero_modulus(double v) { return v == 0.0; }
+__host__ __device__ __forceinline__ bool zero_modulus(dfloat v) { return v.hi == 0.0f && v.lo == 0.0f; }
+
 // Conversions of the 18 planes (N values each) of the load cases in `mask`.
 // (one thread per node and its 18 planes: no per-element division)
 __global__ void to_dfloat_kernel(size_t N, int mask, const double *__restrict__ x, dfloat *__restrict__ y) {

@@ -102,6 +102,7 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
             for (int c = 0; c < 8; ++c) {
                 const size_t e = ((size_t)(2 * Z + (c >> 2)) * rf + (2 * Y + ((c >> 1) & 1))) * rf + (2 * X + (c & 1));
                 const float Ee = rho ? (float)(Ev + rho[e] * (E - Ev)) : (mask[e] ? E : Ev);
+                if (Ee == 0.0f) continue;  // culled child (active set): adds exact zeros
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -245,14 +246,18 @@ __global__ void mg_dinv_fine_kernel(int r, const uint8_t *mask, const double *rh
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         const int ix = n % r, iy = (n / r) % r, iz = n / ((size_t)r * r);
         double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, o[9];
+        bool any = false;
         for (int b = 0; b < 8; ++b) {
             const size_t e = ((size_t)wrap_l(iz - (b >> 2), r) * r + wrap_l(iy - ((b >> 1) & 1), r)) * r +
                              wrap_l(ix - (b & 1), r);
             const double Ee = rho ? Ev + rho[e] * (E - Ev) : (mask[e] ? E : Ev);
+            if (Ee == 0.0) continue;  // culled element (active set): adds exact zeros
+            any = true;
             for (int m = 0; m < 9; ++m) a[m] += Ee * cb.K[b][m];
         }
-        inv3(a, o);
-        for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = n == 0 ? 0.0f : (float)o[m];
+        // a node with no active element has a zero block, whose inverse is zero
+        if (any) inv3(a, o);
+        for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = (n == 0 || !any) ? 0.0f : (float)o[m];
     }
 }
 

@@ -126,19 +126,21 @@ inline int rows_prepare() {
     std::lock_guard<std::mutex> lk(mu);
     if (occ[dev] == 0) {
         const size_t sm = RowShape<R>::template smem<SMOOTH>();
-        int n = 0, n0 = 0;
-        if (cudaFuncSetAttribute(apply_rows_kernel<R, SMOOTH, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm) != cudaSuccess ||
-            cudaFuncSetAttribute(apply_rows_kernel<R, SMOOTH, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, apply_rows_kernel<R, SMOOTH, 0>,
-                                                          RowShape<R>::THREADS, sm) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_rows_kernel<R, SMOOTH, 1>, RowShape<R>::THREADS,
-                                                          sm) != cudaSuccess) {
-            cudaGetLastError();
-            n = 0;
+        // one geometry (and partials layout) for every DOT / CULL variant
+        const void *fns[4] = {(const void *)apply_rows_kernel<R, SMOOTH, 0, false>,
+                              (const void *)apply_rows_kernel<R, SMOOTH, 1, false>,
+                              (const void *)apply_rows_kernel<R, SMOOTH, 0, true>,
+                              (const void *)apply_rows_kernel<R, SMOOTH, 1, true>};
+        int n = 1 << 30;
+        for (const void *f : fns) {
+            int nf = 0;
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nf, f, RowShape<R>::THREADS, sm) != cudaSuccess) {
+                cudaGetLastError();
+                nf = 0;
+            }
+            n = std::min(n, nf);
         }
-        n = std::min(n, n0);  // one geometry (and partials layout) for both DOT variants
         occ[dev] = n > 0 ? n : -1;
     }
     return occ[dev];
@@ -203,10 +205,13 @@ template <int R, bool SMOOTH>
 inline void rows_launch(dim3 g, cudaStream_t s, const ApplyArgs<float> &a, const RowConsts &kc) {
     constexpr int NT = RowShape<R>::THREADS;
     const size_t sm = RowShape<R>::template smem<SMOOTH>();
+    const bool cull = a.Evoid == 0.0f;  // the active set: culled elements carry no stiffness
     if (a.dot == 1)
-        pdl_launch(apply_rows_kernel<R, SMOOTH, 1>, g, NT, sm, s, a, kc);
+        pdl_launch(cull ? apply_rows_kernel<R, SMOOTH, 1, true> : apply_rows_kernel<R, SMOOTH, 1, false>, g, NT, sm,
+                   s, a, kc);
     else
-        pdl_launch(apply_rows_kernel<R, SMOOTH, 0>, g, NT, sm, s, a, kc);
+        pdl_launch(cull ? apply_rows_kernel<R, SMOOTH, 0, true> : apply_rows_kernel<R, SMOOTH, 0, false>, g, NT, sm,
+                   s, a, kc);
 }
 template <int R>
 inline void rows_launch_r(dim3 g, cudaStream_t s, const ApplyArgs<float> &a, const RowConsts &kc) {
@@ -1491,9 +1496,10 @@ inline int run_chom(shl_ctx *ctx, int r, const Density &den, double nu, const do
                     cudaStream_t s, bool df = false) {
     const size_t N = (size_t)r * r * r;
     const int g = grid1d(N, kChomThreads, 148 * 8);
+    const int gdf = (int)std::min<size_t>((N + kChomDfElems - 1) / kChomDfElems, 148 * 6);
     double *partial = nullptr;
     unsigned *ticket = nullptr;
-    SHL_TRY(ws_get_t(ctx, "chom_partial", (size_t)g * 21, &partial));
+    SHL_TRY(ws_get_t(ctx, "chom_partial", (size_t)std::max(g, gdf) * 21, &partial));
     SHL_TRY(ws_get_t(ctx, "chom_ticket", 1, &ticket));
     if (df) {
         ElemOp<dfloat> opd;
@@ -1513,9 +1519,7 @@ inline int run_chom(shl_ctx *ctx, int r, const Density &den, double nu, const do
         a.ticket = ticket;
         a.C = C_dev;
         a.op = opd;
-        const size_t smem = sizeof(dfloat) * 6 * 24 * kChomThreads;
-        raise_smem_limit((const void *)chom_df_kernel, smem);
-        chom_df_kernel<<<g, kChomThreads, smem, s>>>(a);
+        chom_df_kernel<<<gdf, kChomDfThreads, 0, s>>>(a);
         ctx->launches += 2;
         SHL_CUDA(ctx, cudaGetLastError());
         return SHL_OK;
