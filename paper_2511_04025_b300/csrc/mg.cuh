@@ -80,6 +80,49 @@ __device__ inline int wrap_l(int v, int r) { return v < 0 ? v + r : (v >= r ? v 
 // load case has converged (uniform across the grid).
 __device__ inline bool mg_done(const PcgState *st) { return st && st->nactive == 0; }
 
+// Node activity of the active set (Sec. 4.2.1), per level: a fine node is
+// active when one of its 8 elements carries stiffness, a coarse node when one
+// of the fine nodes 2I + a (a in {-1, 0, 1}^3) of its prolongation support is.
+// An inactive node's stencil row and block inverse are exactly zero on every
+// level (every product that forms them sums zeros), so the kernels below can
+// skip it without changing a result.
+__global__ void mg_node_active_fine_kernel(int r, const uint8_t *mask, const double *rho, double E, double Ev,
+                                           uint8_t *act) {
+    const size_t N = (size_t)r * r * r;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int ix = n % r, iy = (n / r) % r, iz = n / ((size_t)r * r);
+        bool any = false;
+        for (int b = 0; b < 8 && !any; ++b) {
+            const size_t e = ((size_t)wrap_l(iz - (b >> 2), r) * r + wrap_l(iy - ((b >> 1) & 1), r)) * r +
+                             wrap_l(ix - (b & 1), r);
+            any = (rho ? Ev + rho[e] * (E - Ev) : (mask[e] ? E : Ev)) != 0.0;
+        }
+        act[n] = any ? 1 : 0;
+    }
+}
+__global__ void mg_node_active_coarse_kernel(int rc, const uint8_t *__restrict__ act_f, uint8_t *__restrict__ act_c) {
+    const size_t Nc = (size_t)rc * rc * rc;
+    const int rf = 2 * rc;
+    for (size_t I = blockIdx.x * (size_t)blockDim.x + threadIdx.x; I < Nc; I += (size_t)gridDim.x * blockDim.x) {
+        const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
+        bool any = false;
+        for (int a = 0; a < 27 && !any; ++a)
+            any = act_f[((size_t)wrap_l(2 * iz + a / 9 - 1, rf) * rf + wrap_l(2 * iy + (a / 3) % 3 - 1, rf)) * rf +
+                        wrap_l(2 * ix + a % 3 - 1, rf)] != 0;
+        act_c[I] = any ? 1 : 0;
+    }
+}
+// blk[b] = 1 when one of the nodes 32 b .. 32 b + 31 is active (the node
+// groups of mg_stencil_nc_kernel)
+__global__ void mg_block_active_kernel(size_t N, const uint8_t *__restrict__ act, uint8_t *__restrict__ blk) {
+    const size_t nb = (N + 31) / 32;
+    for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < nb; b += (size_t)gridDim.x * blockDim.x) {
+        bool any = false;
+        for (size_t n = 32 * b; n < min(N, 32 * b + 32) && !any; ++n) any = act[n] != 0;
+        blk[b] = any ? 1 : 0;
+    }
+}
+
 // Level 1 stencil from the fine elements.  Thread = (coarse node I, offset delta).
 // Mc: the 8 child matrices P_c^T K_unit P_c (unit modulus, unit element),
 // [8][24][24] floats in device memory (per context, uploaded at setup).
@@ -121,7 +164,10 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
 // the same order as a thread per block would: the rounding of these sums
 // decides whether a mode held only by the ersatz void stays resolvable on
 // the coarsest level, so it is kept fixed).
-__global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc) {
+// ACT (the active set): skip inactive coarse nodes and inactive fine neighbours.
+template <bool ACT>
+__global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc,
+                                          const uint8_t *__restrict__ act_f, const uint8_t *__restrict__ act_c) {
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27 * 9; t += (size_t)gridDim.x * blockDim.x) {
@@ -132,12 +178,17 @@ __global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, 
         const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
         const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
         float acc = 0.0f;
+        if (ACT && !act_c[I]) {  // inactive coarse node (active set): a zero row
+            Sc[t] = 0.0f;
+            continue;
+        }
         for (int az = -1; az <= 1; ++az)
             for (int ay = -1; ay <= 1; ++ay)
                 for (int ax = -1; ax <= 1; ++ax) {
                     const float wa = tri_w(ax, ay, az);
                     const size_t fi =
                         ((size_t)wrap_l(2 * iz + az, rf) * rf + wrap_l(2 * iy + ay, rf)) * rf + wrap_l(2 * ix + ax, rf);
+                    if (ACT && !act_f[fi]) continue;  // an inactive fine node's row is zero
                     for (int bz = -1; bz <= 1; ++bz)
                         for (int by = -1; by <= 1; ++by)
                             for (int bx = -1; bx <= 1; ++bx) {
@@ -225,8 +276,12 @@ __host__ __device__ inline void spd_inv3(const double a_in[9], double o[9]) {
 }
 
 // Block-Jacobi inverse of a stencil level (center block), SPD by construction.
-__global__ void mg_dinv_stencil_kernel(size_t N, const float *S, float *Dinv) {
+__global__ void mg_dinv_stencil_kernel(size_t N, const float *S, float *Dinv, const uint8_t *act) {
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        if (act && !act[n]) {  // inactive node (active set): zero block, zero inverse
+            for (int m = 0; m < 9; ++m) Dinv[(size_t)m * N + n] = 0.0f;
+            continue;
+        }
         double a[9], o[9];
         for (int m = 0; m < 9; ++m) a[m] = S[(n * 27 + 13) * 9 + m];
         spd_inv3(a, o);
@@ -421,18 +476,32 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int r, const float *__r
 // distinct bank groups), with three coalesced loads of x per offset.  The
 // sums are formed in the same order as with one block at a time.
 constexpr int kStencilNodes = 32, kStencilPitch = 244;
+// ACT (the active set): node groups whose blk byte is 0 take the short path.
+template <bool ACT>
 __global__ void __launch_bounds__(6 * kStencilNodes) mg_stencil_nc_kernel(int r, const float *__restrict__ S,
                                                                         const float *__restrict__ x,
                                                                         const float *__restrict__ b,
                                                                         const float *__restrict__ Dinv, float w,
                                                                         int mode, float *__restrict__ out,
-                                                                        const PcgState *st) {
+                                                                        const PcgState *st,
+                                                                        const uint8_t *__restrict__ blk) {
     __shared__ __align__(16) float sS[kStencilNodes * kStencilPitch];
     pdl_enter();
     if (mg_done(st)) return;
     const unsigned N = (unsigned)r * r * r;
     const unsigned n0 = blockIdx.x * kStencilNodes;
     const unsigned nn = min((unsigned)kStencilNodes, N - n0);
+    if (ACT && !blk[blockIdx.x]) {
+        // 32 inactive nodes (active set): zero rows and zero block inverses,
+        // so A x = 0 there and the pass reduces to mode 0: 0, 1: b, 2: x
+        const int k = threadIdx.x / kStencilNodes, lane = threadIdx.x % kStencilNodes;
+        if ((unsigned)lane >= nn || (st && !st->active[k])) return;
+        const size_t o = (size_t)(3 * k) * N + n0 + lane;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            out[o + (size_t)c * N] = mode == 0 ? 0.0f : (mode == 1 ? b[o + (size_t)c * N] : x[o + (size_t)c * N]);
+        return;
+    }
     {
         // 16-byte loads (n0 * 243 floats is a multiple of 4: n0 is a multiple of 32), scattered to the pitch
         const unsigned cnt = nn * 243;

@@ -831,6 +831,9 @@ struct MgLevel {
     float *Dinv = nullptr;  // 3x3 block-Jacobi inverses
     float *x = nullptr, *b = nullptr, *t = nullptr;
     float *xa = nullptr, *xb = nullptr;  // ping-pong iterate buffers (levels >= 1)
+    // active set only (null otherwise): node activity, and per group of 32
+    // nodes whether one is active (levels run by mg_stencil_nc_kernel)
+    uint8_t *act = nullptr, *blk = nullptr;
 };
 
 struct Mg {
@@ -879,8 +882,9 @@ inline int mg_child_matrices(shl_ctx *ctx, double nu, cudaStream_t s, float **ou
 inline void launch_stencil(const MgLevel &L, const float *x, const float *b, float w, int mode, float *out,
                            const PcgState *st, cudaStream_t s) {
     if (L.N >= 32768)
-        pdl_launch(mg_stencil_nc_kernel, (unsigned)((L.N + kStencilNodes - 1) / kStencilNodes), 6 * kStencilNodes, 0, s,
-                   L.r, (const float *)L.S, x, b, (const float *)L.Dinv, w, mode, out, st);
+        pdl_launch(L.blk ? mg_stencil_nc_kernel<true> : mg_stencil_nc_kernel<false>,
+                   (unsigned)((L.N + kStencilNodes - 1) / kStencilNodes), 6 * kStencilNodes, 0, s, L.r,
+                   (const float *)L.S, x, b, (const float *)L.Dinv, w, mode, out, st, (const uint8_t *)L.blk);
     else
         pdl_launch(mg_stencil_kernel, grid1d(32 * L.N, kBlk, 148 * 16), kBlk, 0, s, L.r, (const float *)L.S, x, b,
                    (const float *)L.Dinv, w, mode, out, st);
@@ -911,6 +915,26 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             SHL_TRY(ws_get_t(ctx, nm, L.N * 18, &L.b));
         }
     }
+    // active set: node activity per level, node groups of the streaming stencil passes
+    for (int l = 0; l <= mg->L; ++l) mg->lv[l].act = mg->lv[l].blk = nullptr;
+    if (den.Ev == 0.0) {
+        for (int l = 0; l <= mg->L; ++l) {
+            MgLevel &L = mg->lv[l];
+            snprintf(nm, sizeof(nm), "mg_act%d", l);
+            SHL_TRY(ws_get_t(ctx, nm, L.N, &L.act));
+            if (l == 0)
+                mg_node_active_fine_kernel<<<grid1d(L.N), kBlk, 0, s>>>(r, den.mask, den.rho, den.E, den.Ev, L.act);
+            else
+                mg_node_active_coarse_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, mg->lv[l - 1].act, L.act);
+            ++ctx->launches;
+            if (l >= 1 && L.N >= 32768) {
+                snprintf(nm, sizeof(nm), "mg_blk%d", l);
+                SHL_TRY(ws_get_t(ctx, nm, (L.N + 31) / 32, &L.blk));
+                mg_block_active_kernel<<<grid1d((L.N + 31) / 32), kBlk, 0, s>>>(L.N, L.act, L.blk);
+                ++ctx->launches;
+            }
+        }
+    }
     // fine block-Jacobi
     double Ku[24][24];
     unit_hex8_stiffness(o->nu, Ku);
@@ -927,9 +951,11 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         if (l == 1)
             mg_galerkin_fine_kernel<<<g, kBlk, 0, s>>>(L.r, den.mask, den.rho, (float)den.E, (float)den.Ev,
                                                        (float)(1.0 / r), childM, L.S);
+        else if (L.act)
+            mg_galerkin_coarse_kernel<true><<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S, mg->lv[l - 1].act, L.act);
         else
-            mg_galerkin_coarse_kernel<<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S);
-        mg_dinv_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.N, L.S, L.Dinv);
+            mg_galerkin_coarse_kernel<false><<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S, nullptr, nullptr);
+        mg_dinv_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.N, L.S, L.Dinv, L.act);
         ctx->launches += 2;
     }
     SHL_CUDA(ctx, cudaGetLastError());
@@ -1020,7 +1046,10 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         return SHL_OK;
         };
         IterGraph pg;
-        SHL_TRY(capture_iteration(ctx, s, &pg, power, "mgpow_" + std::to_string(r) + (den.rho ? "_s" : "_m")));
+        // one cached graph per grid, density kind and void model (the active
+        // set launches other kernel variants, so the two do not update in place)
+        SHL_TRY(capture_iteration(ctx, s, &pg, power,
+                                  "mgpow_" + std::to_string(r) + (den.rho ? "_s" : "_m") + (den.Ev == 0.0 ? "_a" : "")));
         SHL_TRY(replay(ctx, s, &pg, 1));
         SHL_CUDA(ctx, cudaMemcpyAsync(hpw, pw, (size_t)mg->L * kPow * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
@@ -1404,7 +1433,8 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
             };
             IterGraph graph;
             SHL_TRY(capture_iteration(ctx, s, &graph, iteration,
-                                      "pcg32_" + std::to_string(r) + (use_mg ? "_mg" : "_jacobi")));
+                                      "pcg32_" + std::to_string(r) + (use_mg ? "_mg" : "_jacobi") +
+                                          (den.Ev == 0.0 ? "_a" : "")));
             PcgState hst;
             for (long long it = 0;; it += chunk) {
                 if (it > (long long)maxit + 2 * chunk)
