@@ -46,10 +46,10 @@ APPLY_BYTES_PER_NODE_F32 = 72 + 72 + 1  # read p (18 floats), write q (18 floats
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per launch of the FP32 stiffness apply at 64^3
 # (the row kernel), from one `ncu --set full` capture of
-# `bench.py --kernel apply --r 64`: reads 19,177,216 B (p and the mask, the
+# `bench.py --kernel apply --r 64`: reads 19,177,472 B (p and the mask, the
 # algorithmic minimum) + 0 B written (q's writes were still in L2 when the
 # captured launch ended).  Reset to None whenever the kernel changes.
-APPLY_TRAFFIC_64 = 19_177_216
+APPLY_TRAFFIC_64 = 19_177_472
 
 
 def peaks():
