@@ -66,7 +66,11 @@ inline void raise_smem_limit(const void *fn, size_t bytes) {
 
 // Launch with programmatic stream serialisation (the kernel starts with
 // pdl_enter(): it waits for the preceding kernel before touching memory, and
-// its launch overlaps that kernel's tail).
+// its launch overlaps that kernel's tail).  SHL_PDL=0 at compile time makes
+// these ordinary launches.
+#ifndef SHL_PDL
+#define SHL_PDL 1
+#endif
 template <typename... KArgs, typename... Args>
 inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args &&...args) {
@@ -77,7 +81,7 @@ inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[0].val.programmaticStreamSerializationAllowed = SHL_PDL;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
