@@ -159,46 +159,61 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
 
 // Level l+1 stencil from level l (Galerkin with trilinear P):
 //   Sc(I, delta) = sum_a sum_b w(a) w(a + b - 2 delta) Sf(2I + a, b).
-// Thread = (I, delta, entry m): the coarse levels are small, so the nine
-// entries of a block go to nine threads (each sums its entry over (a, b) in
-// the same order as a thread per block would: the rounding of these sums
-// decides whether a mode held only by the ersatz void stays resolvable on
-// the coarsest level, so it is kept fixed).
+// Block = one coarse node I: the stencils of the 27 fine nodes 2I + a of its
+// prolongation support (27 x 243 floats) are staged in shared memory once,
+// and thread (delta, entry m) sums its entry from there over (a, b) in the
+// same order as a thread per block would (the rounding of these sums decides
+// whether a mode held only by the ersatz void stays resolvable on the
+// coarsest level, so it is kept fixed).
 // ACT (the active set): skip inactive coarse nodes and inactive fine neighbours.
+constexpr int kGalerkinThreads = 256;  // 243 entries of a coarse node's stencil
 template <bool ACT>
-__global__ void mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc,
-                                          const uint8_t *__restrict__ act_f, const uint8_t *__restrict__ act_c) {
+__global__ void __launch_bounds__(kGalerkinThreads)
+    mg_galerkin_coarse_kernel(int rc, const float *__restrict__ Sf, float *__restrict__ Sc,
+                              const uint8_t *__restrict__ act_f, const uint8_t *__restrict__ act_c) {
+    __shared__ float sf[27 * 243];
+    __shared__ uint8_t sact[27];
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27 * 9; t += (size_t)gridDim.x * blockDim.x) {
-        const int m = (int)(t % 9);
-        const size_t Id = t / 9;
-        const size_t I = Id / 27;
-        const int dl = (int)(Id % 27);
-        const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+    for (size_t I = blockIdx.x; I < Nc; I += gridDim.x) {  // uniform per block
         const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
-        float acc = 0.0f;
         if (ACT && !act_c[I]) {  // inactive coarse node (active set): a zero row
-            Sc[t] = 0.0f;
+            for (int t = threadIdx.x; t < 243; t += blockDim.x) Sc[I * 243 + t] = 0.0f;
             continue;
         }
-        for (int az = -1; az <= 1; ++az)
-            for (int ay = -1; ay <= 1; ++ay)
-                for (int ax = -1; ax <= 1; ++ax) {
-                    const float wa = tri_w(ax, ay, az);
-                    const size_t fi =
-                        ((size_t)wrap_l(2 * iz + az, rf) * rf + wrap_l(2 * iy + ay, rf)) * rf + wrap_l(2 * ix + ax, rf);
-                    if (ACT && !act_f[fi]) continue;  // an inactive fine node's row is zero
-                    for (int bz = -1; bz <= 1; ++bz)
-                        for (int by = -1; by <= 1; ++by)
-                            for (int bx = -1; bx <= 1; ++bx) {
-                                const float wb = tri_w(ax + bx - 2 * dx, ay + by - 2 * dy, az + bz - 2 * dz);
-                                if (wb == 0.0f) continue;
-                                const int bl = (bz + 1) * 9 + (by + 1) * 3 + (bx + 1);
-                                acc += (wa * wb) * __ldg(Sf + (fi * 27 + bl) * 9 + m);
-                            }
-                }
-        Sc[Id * 9 + m] = acc;
+        auto fine = [&](int a) -> size_t {  // fine node 2I + a, a = (az + 1) 9 + (ay + 1) 3 + (ax + 1)
+            return ((size_t)wrap_l(2 * iz + a / 9 - 1, rf) * rf + wrap_l(2 * iy + (a / 3) % 3 - 1, rf)) * rf +
+                   wrap_l(2 * ix + a % 3 - 1, rf);
+        };
+        __syncthreads();  // the previous node's reads of sf are done
+        for (int k = threadIdx.x; k < 27 * 243; k += blockDim.x) {
+            const int a = k / 243;
+            const size_t fi = fine(a);
+            sf[k] = (ACT && !act_f[fi]) ? 0.0f : __ldg(Sf + fi * 243 + (k - a * 243));
+        }
+        if (threadIdx.x < 27) sact[threadIdx.x] = ACT ? act_f[fine(threadIdx.x)] : 1;
+        __syncthreads();
+        if (threadIdx.x < 243) {
+            const int t = threadIdx.x, m = t % 9, dl = t / 9;
+            const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+            float acc = 0.0f;
+            for (int az = -1; az <= 1; ++az)
+                for (int ay = -1; ay <= 1; ++ay)
+                    for (int ax = -1; ax <= 1; ++ax) {
+                        const float wa = tri_w(ax, ay, az);
+                        const int a = (az + 1) * 9 + (ay + 1) * 3 + (ax + 1);
+                        if (ACT && !sact[a]) continue;  // an inactive fine node's row is zero
+                        for (int bz = -1; bz <= 1; ++bz)
+                            for (int by = -1; by <= 1; ++by)
+                                for (int bx = -1; bx <= 1; ++bx) {
+                                    const float wb = tri_w(ax + bx - 2 * dx, ay + by - 2 * dy, az + bz - 2 * dz);
+                                    if (wb == 0.0f) continue;
+                                    const int bl = (bz + 1) * 9 + (by + 1) * 3 + (bx + 1);
+                                    acc += (wa * wb) * sf[a * 243 + bl * 9 + m];
+                                }
+                    }
+            Sc[I * 243 + t] = acc;
+        }
     }
 }
 

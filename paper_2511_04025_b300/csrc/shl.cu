@@ -951,14 +951,17 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
     ++ctx->launches;
     for (int l = 1; l <= mg->L; ++l) {
         MgLevel &L = mg->lv[l];
-        const int g = grid1d(L.N * 27 * (l == 1 ? 1 : 9), kBlk, 148 * 16);  // coarse-from-coarse: a thread per entry
+        const int g = grid1d(L.N * 27, kBlk, 148 * 16);
+        const int gc = (int)std::min<size_t>(L.N, 148 * 8);  // coarse-from-coarse: a block per coarse node
         if (l == 1)
             mg_galerkin_fine_kernel<<<g, kBlk, 0, s>>>(L.r, den.mask, den.rho, (float)den.E, (float)den.Ev,
                                                        (float)(1.0 / r), childM, L.S);
         else if (L.act)
-            mg_galerkin_coarse_kernel<true><<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S, mg->lv[l - 1].act, L.act);
+            mg_galerkin_coarse_kernel<true><<<gc, kGalerkinThreads, 0, s>>>(L.r, mg->lv[l - 1].S, L.S,
+                                                                           mg->lv[l - 1].act, L.act);
         else
-            mg_galerkin_coarse_kernel<false><<<g, kBlk, 0, s>>>(L.r, mg->lv[l - 1].S, L.S, nullptr, nullptr);
+            mg_galerkin_coarse_kernel<false><<<gc, kGalerkinThreads, 0, s>>>(L.r, mg->lv[l - 1].S, L.S, nullptr,
+                                                                            nullptr);
         mg_dinv_stencil_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.N, L.S, L.Dinv, L.act);
         ctx->launches += 2;
     }
