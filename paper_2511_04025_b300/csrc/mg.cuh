@@ -127,7 +127,7 @@ __global__ void mg_block_active_kernel(size_t N, const uint8_t *__restrict__ act
 // Mc: the 8 child matrices P_c^T K_unit P_c (unit modulus, unit element),
 // [8][24][24] floats in device memory (per context, uploaded at setup).
 __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const double *rho, float E, float Ev, float h,
-                                        const float *__restrict__ Mc, float *S) {
+                                        const float *__restrict__ Mc, float *S, const uint8_t *act_c) {
     const size_t Nc = (size_t)rc * rc * rc;
     const int rf = 2 * rc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < Nc * 27; t += (size_t)gridDim.x * blockDim.x) {
@@ -136,6 +136,11 @@ __global__ void mg_galerkin_fine_kernel(int rc, const uint8_t *mask, const doubl
         const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
         const int ix = I % rc, iy = (I / rc) % rc, iz = I / ((size_t)rc * rc);
         float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (act_c && !act_c[I]) {  // inactive coarse node (active set): every child culled, a zero row
+#pragma unroll
+            for (int m = 0; m < 9; ++m) S[(I * 27 + dl) * 9 + m] = 0.0f;
+            continue;
+        }
         for (int A = 0; A < 8; ++A) {
             const int ax = A & 1, ay = (A >> 1) & 1, az = A >> 2;
             const int bx = ax + dx, by = ay + dy, bz = az + dz;
@@ -631,7 +636,7 @@ __device__ __forceinline__ float restrict_plane(const float *__restrict__ bm, co
 // cases are skipped.
 __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *__restrict__ bf,
                                                           const float *__restrict__ tf, float *__restrict__ bc,
-                                                          const PcgState *st) {
+                                                          const PcgState *st, const uint8_t *__restrict__ act_c) {
     pdl_enter();
     if (mg_done(st)) return;
     const int m = blockIdx.y;
@@ -650,6 +655,11 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *_
         const unsigned I = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
         const bool valid = I < Nc;
         const unsigned Iv = valid ? I : 0;
+        // a warp of inactive coarse nodes (active set) restricts zeros
+        if (act_c && __all_sync(0xffffffffu, !valid || !act_c[Iv])) {
+            if (valid) bc[(size_t)m * Nc + I] = 0.0f;
+            continue;
+        }
         const int ix = (int)(Iv % (unsigned)rc), iy = (int)((Iv / (unsigned)rc) % (unsigned)rc),
                   iz = (int)(Iv / ((unsigned)rc * rc));
         const unsigned zo[3] = {(unsigned)wrap_l(2 * iz - 1, rf) * rrf, (unsigned)(2 * iz) * rrf,
@@ -668,7 +678,8 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(int rc, const float *_
 __global__ void __launch_bounds__(256) mg_restrict_jacobi_kernel(int rc, const float *__restrict__ bf,
                                                                  const float *__restrict__ tf, float *__restrict__ bc,
                                                                  const float *__restrict__ Dc, float w,
-                                                                 float *__restrict__ xc, const PcgState *st) {
+                                                                 float *__restrict__ xc, const PcgState *st,
+                                                                 const uint8_t *__restrict__ act_c) {
     pdl_enter();
     if (mg_done(st)) return;
     const int k = blockIdx.y;
@@ -684,6 +695,18 @@ __global__ void __launch_bounds__(256) mg_restrict_jacobi_kernel(int rc, const f
         const unsigned I = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
         const bool valid = I < Nc;
         const unsigned Iv = valid ? I : 0;
+        // a warp of inactive coarse nodes (active set): zero restriction, zero
+        // block inverses, so b and x are zero there
+        if (act_c && __all_sync(0xffffffffu, !valid || !act_c[Iv])) {
+            if (valid)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const size_t o = (size_t)(3 * k + i) * Nc + I;
+                    bc[o] = 0.0f;
+                    xc[o] = 0.0f;
+                }
+            continue;
+        }
         const int ix = (int)(Iv % (unsigned)rc), iy = (int)((Iv / (unsigned)rc) % (unsigned)rc),
                   iz = (int)(Iv / ((unsigned)rc * rc));
         const unsigned zo[3] = {(unsigned)wrap_l(2 * iz - 1, rf) * rrf, (unsigned)(2 * iz) * rrf,
@@ -715,7 +738,8 @@ __global__ void __launch_bounds__(256) mg_restrict_jacobi_kernel(int rc, const f
 // Converged load cases are skipped; with pin0 the fine node 0 (pinned) is
 // left unchanged.
 __global__ void __launch_bounds__(256) mg_prolong_kernel(int rc, const float *__restrict__ xc,
-                                                         float *__restrict__ xf, int pin0, const PcgState *st) {
+                                                         float *__restrict__ xf, int pin0, const PcgState *st,
+                                                         const uint8_t *__restrict__ act_c) {
     pdl_enter();
     if (mg_done(st)) return;
     const int m = blockIdx.y;
@@ -728,6 +752,10 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(int rc, const float *__
         const int cx = (int)(I % (unsigned)rc), cy = (int)((I / (unsigned)rc) % (unsigned)rc), cz = (int)(I / rrc);
         const unsigned x1 = (unsigned)wrap_l(cx + 1, rc), y0 = (unsigned)cy * rc, y1 = (unsigned)wrap_l(cy + 1, rc) * rc,
                        z0 = (unsigned)cz * rrc, z1 = (unsigned)wrap_l(cz + 1, rc) * rrc;
+        // a coarse cell whose 8 corners are inactive (active set) holds x = 0: nothing to add
+        if (act_c && !(act_c[z0 + y0 + cx] | act_c[z0 + y0 + x1] | act_c[z0 + y1 + cx] | act_c[z0 + y1 + x1] |
+                       act_c[z1 + y0 + cx] | act_c[z1 + y0 + x1] | act_c[z1 + y1 + cx] | act_c[z1 + y1 + x1]))
+            continue;
         float e[2][2][2];  // [c][b][x]: the cell's values combined along z and y
 #pragma unroll
         for (int xi = 0; xi < 2; ++xi) {

@@ -955,7 +955,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
         const int gc = (int)std::min<size_t>(L.N, 148 * 8);  // coarse-from-coarse: a block per coarse node
         if (l == 1)
             mg_galerkin_fine_kernel<<<g, kBlk, 0, s>>>(L.r, den.mask, den.rho, (float)den.E, (float)den.Ev,
-                                                       (float)(1.0 / r), childM, L.S);
+                                                       (float)(1.0 / r), childM, L.S, L.act);
         else if (L.act)
             mg_galerkin_coarse_kernel<true><<<gc, kGalerkinThreads, 0, s>>>(L.r, mg->lv[l - 1].S, L.S,
                                                                            mg->lv[l - 1].act, L.act);
@@ -1213,9 +1213,10 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
         MgLevel &Cl = mg->lv[l + 1];
         if (l + 1 < mg->L)
             pdl_launch(mg_restrict_jacobi_kernel, dim3(grid1d(Cl.N, kBlk, 148), 6), kBlk, 0, s, Cl.r, bf, tf, Cl.b,
-                       (const float *)Cl.Dinv, l + 1 >= 2 ? Cl.wk[0] : Cl.omega, Cl.x, st);
+                       (const float *)Cl.Dinv, l + 1 >= 2 ? Cl.wk[0] : Cl.omega, Cl.x, st, (const uint8_t *)Cl.act);
         else
-            pdl_launch(mg_restrict_kernel, dim3(grid1d(Cl.N, kBlk, 148), 18), kBlk, 0, s, Cl.r, bf, tf, Cl.b, st);
+            pdl_launch(mg_restrict_kernel, dim3(grid1d(Cl.N, kBlk, 148), 18), kBlk, 0, s, Cl.r, bf, tf, Cl.b, st,
+                       (const uint8_t *)Cl.act);
         ++ctx->launches;
     };
     // fine level: pre-smoothing and the restriction of its residual
@@ -1256,7 +1257,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
         cycle(l + 1, true);
         for (int v = 1; v < visits; ++v) cycle(l + 1, false);
         pdl_launch(mg_prolong_kernel, dim3(grid1d(mg->lv[l + 1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[l + 1].r,
-                   mg->lv[l + 1].x, L.x, 0, st);
+                   mg->lv[l + 1].x, L.x, 0, st, (const uint8_t *)mg->lv[l + 1].act);
         ++ctx->launches;
         for (int it = 0; it < nu; ++it) sweep(L, 2, l >= 2 ? L.wk[nu - 1 - it] : -1.0f);
     };
@@ -1266,7 +1267,7 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
         MgLevel &L = mg->lv[0];
         const int g = grid1d(L.N);
         pdl_launch(mg_prolong_kernel, dim3(grid1d(mg->lv[1].N, kBlk, 148), 18), kBlk, 0, s, mg->lv[1].r,
-                   mg->lv[1].x, L.x, 1, st);
+                   mg->lv[1].x, L.x, 1, st, (const uint8_t *)mg->lv[1].act);
         ++ctx->launches;
         for (int it = 0; it < mg->nu; ++it) {
             SHL_TRY(fine_apply(L.x, L.t));
