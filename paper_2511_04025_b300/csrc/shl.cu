@@ -879,13 +879,20 @@ inline int mg_child_matrices(shl_ctx *ctx, double nu, cudaStream_t s, float **ou
     return SHL_OK;
 }
 
+// Smallest level (nodes) whose stencil passes run a thread per (node, load
+// case); smaller levels run a warp per node.
+#ifndef SHL_NC_MIN_NODES
+#define SHL_NC_MIN_NODES 32768
+#endif
+constexpr size_t kStencilNcMinNodes = SHL_NC_MIN_NODES;
+
 // Stencil pass on one coarse level: one thread per (node, load case) with the
 // stencils staged in shared memory from 32^3 nodes up (bandwidth and issue
 // bound), one warp per node below (latency bound: few nodes, and the warp form
 // keeps more loads in flight per node).  The caller counts the launch.
 inline void launch_stencil(const MgLevel &L, const float *x, const float *b, float w, int mode, float *out,
                            const PcgState *st, cudaStream_t s) {
-    if (L.N >= 32768)
+    if (L.N >= kStencilNcMinNodes)
         pdl_launch(L.blk ? mg_stencil_nc_kernel<true> : mg_stencil_nc_kernel<false>,
                    (unsigned)((L.N + kStencilNodes - 1) / kStencilNodes), 6 * kStencilNodes, 0, s, L.r,
                    (const float *)L.S, x, b, (const float *)L.Dinv, w, mode, out, st, (const uint8_t *)L.blk);
@@ -931,7 +938,7 @@ inline int mg_setup(shl_ctx *ctx, int r, const Density &den, const shl_solve_opt
             else
                 mg_node_active_coarse_kernel<<<grid1d(L.N), kBlk, 0, s>>>(L.r, mg->lv[l - 1].act, L.act);
             ++ctx->launches;
-            if (l >= 1 && L.N >= 32768) {
+            if (l >= 1 && L.N >= kStencilNcMinNodes) {
                 snprintf(nm, sizeof(nm), "mg_blk%d", l);
                 SHL_TRY(ws_get_t(ctx, nm, (L.N + 31) / 32, &L.blk));
                 mg_block_active_kernel<<<grid1d((L.N + 31) / 32), kBlk, 0, s>>>(L.N, L.act, L.blk);
