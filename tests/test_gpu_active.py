@@ -134,3 +134,18 @@ def test_chom_culled_void_matches_oracle(ctx):
     C = shl.shl_chom(ctx, r, torch.tensor(oracle.aos_to_soa(u), device=DEV),
                      mask=torch.tensor(m, device=DEV), E_void=0.0)
     assert np.abs(C - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("r", [64, 128])
+def test_thin_shell_active_set_multigrid_matches_fp64(ctx, r):
+    """The timing table's thin shell (t = 0.02) with the active set: the FP32 +
+    refinement solve, whose multigrid skips inactive nodes on every level,
+    against the FP64 point-Jacobi solve of the same culled problem (no
+    multigrid), both to a relative residual of 1e-10."""
+    d = inputs.shell_256(0)
+    o32 = shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP32_REFINE, active=1)
+    o64 = shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP64, active=1, max_iter=100000)
+    C32, s32 = shl.shl_homogenize(ctx, d, r, o32)
+    C64, s64 = shl.shl_homogenize(ctx, d, r, o64)
+    assert s32["status"] == 0 and s64["status"] == 0 and s32["precond"] == shl.SHL_PRECOND_MG
+    assert entry_err(C32, C64) <= 1e-9
