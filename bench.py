@@ -699,8 +699,8 @@ def bench_field256(h, stream):
 
 
 def bench_serve_short(args, n_requests=128):
-    """A short serving pass on the serving workload's mix (Poisson stream of
-    --serve with fewer requests): burst throughput X, then Poisson arrivals at
+    """A serving pass on the serving workload's mix (the Poisson stream of
+    --serve, n_requests of it): burst throughput X, then Poisson arrivals at
     0.7 X; p50/p99 latency (submit -> result) overall and at 64^3."""
     import torch
     from paper_2511_04025_b300 import inputs, shl
@@ -988,7 +988,7 @@ def main():
         plain32 = bench_plain32(h, stream)
         grad64 = bench_grad64(h, stream)
         field256 = bench_field256(h, stream)
-        serve = bench_serve_short(args)
+        serve = bench_serve_short(args, n_requests=512)  # the serving workload's 512 requests
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
