@@ -121,9 +121,11 @@ typedef struct {
  *   precond        SHL_PRECOND_MG (default): geometric multigrid V-cycle
  *                  (Sec. 4.2: 2x2x2 coarsening, Galerkin coarse operators,
  *                  damped block-Jacobi smoothing, pinned dense solve on the
- *                  coarsest level) in FP32, used in SHL_FP32_REFINE mode when r
- *                  halves down to a coarsest grid of at most 6^3 nodes;
- *                  otherwise, and in SHL_FP64 mode, point Jacobi.
+ *                  coarsest level) in FP32, used when r halves down to a
+ *                  coarsest grid of at most 6^3 nodes (in SHL_FP64 mode it
+ *                  preconditions FP64 CG: the residual is rounded to FP32 for
+ *                  the V-cycle and the correction widened back); otherwise,
+ *                  or with SHL_PRECOND_JACOBI, point Jacobi.
  *   mg_nu          smoothing sweeps before and after the coarse correction on
  *                  the fine level and the first coarse level (<= 0: 1)
  *   mg_nu_coarse   the same on the smaller levels (index >= 2, at most 1/64 of
@@ -238,8 +240,8 @@ int shl_chom(shl_ctx *ctx, int32_t r, const uint8_t *mask_dev, const double *rho
 
 /*
  * Solve the six periodic cell problems for a given density (node 0 pinned,
- * Jacobi-preconditioned CG on all six load cases at once, per-case
- * convergence and skip) and return C^H.  u_dev (18 SoA planes of doubles, may
+ * preconditioned CG on all six load cases at once -- o->precond, multigrid by
+ * default -- with per-case convergence and skip) and return C^H.  u_dev (18 SoA planes of doubles, may
  * be NULL) receives the displacements; if o->warm_start it also supplies the
  * initial guess.
  */

@@ -249,6 +249,29 @@ __global__ void pcg_init_kernel(VecArgs<T> a, int want_mask, int set_bnorm) {
     }
 }
 
+// ---- FP64 CG with the FP32 multigrid preconditioner ------------------------
+// out = float(in) / out = double(in) on the 18 planes of the active load
+// cases (all six when st is null): the residual goes to the FP32 V-cycle and
+// its result comes back, while the CG recurrences stay FP64.
+__global__ void cvt_f64_f32_kernel(size_t N, const PcgState *st, const double *__restrict__ in,
+                                   float *__restrict__ out) {
+    pdl_enter();
+    if (st && st->nactive == 0) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 18 * N; i += (size_t)gridDim.x * blockDim.x) {
+        if (st && !st->active[i / (3 * N)]) continue;
+        out[i] = (float)in[i];
+    }
+}
+__global__ void cvt_f32_f64_kernel(size_t N, const PcgState *st, const float *__restrict__ in,
+                                   double *__restrict__ out) {
+    pdl_enter();
+    if (st && st->nactive == 0) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 18 * N; i += (size_t)gridDim.x * blockDim.x) {
+        if (st && !st->active[i / (3 * N)]) continue;
+        out[i] = (double)in[i];
+    }
+}
+
 // ---- mixed precision: reliable updates -------------------------------------
 //
 // The FP32 PCG keeps its Krylov direction; every time its recurrence

@@ -626,15 +626,13 @@ inline void launch_vec_update(shl_ctx *ctx, const VecArgs<T> &va, const VecGeom 
     constexpr int VW = (int)(16 / sizeof(T));
     pdl_launch(pcg_alpha_kernel, 1, kVecThreads, 0, s, va.st, ad);
     ++ctx->launches;
-    if constexpr (std::is_same<T, float>::value) {
-        if (mg) {
-            if (g.V == VW)
-                pdl_launch(vec_update_kernel<T, VW, true>, g.blocks(), kVecThreads, 0, s, va, g, fj);
-            else
-                pdl_launch(vec_update_kernel<T, 1, true>, g.blocks(), kVecThreads, 0, s, va, g, fj);
-            ++ctx->launches;
-            return;
-        }
+    if (mg) {  // also writes the first fine pre-smoothing step z = w D^-1 r (FP32)
+        if (g.V == VW)
+            pdl_launch(vec_update_kernel<T, VW, true>, g.blocks(), kVecThreads, 0, s, va, g, fj);
+        else
+            pdl_launch(vec_update_kernel<T, 1, true>, g.blocks(), kVecThreads, 0, s, va, g, fj);
+        ++ctx->launches;
+        return;
     }
     if (g.V == VW)
         pdl_launch(vec_update_kernel<T, VW, false>, g.blocks(), kVecThreads, 0, s, va, g, fj);
@@ -1287,6 +1285,71 @@ inline int mg_vcycle(shl_ctx *ctx, Mg *mg, const ApplyArgs<float> &fine, const f
     return SHL_OK;
 }
 
+// FP64 PCG preconditioned by the FP32 multigrid V-cycle (SHL_FP64 with
+// SHL_PRECOND_MG): per iteration q = K p and the x, r updates in FP64 (the
+// update also takes the V-cycle's first fine smoothing step in FP32), r is
+// rounded to FP32 for the V-cycle, the correction z comes back to FP64, and
+// r.z, beta and the direction p = z + beta p are FP64.  The V-cycle is a
+// fixed symmetric operator, so this is ordinary PCG with an FP32-accurate
+// preconditioner; convergence is judged on FP64 residuals.
+inline int pcg_run_mg64(shl_ctx *ctx, int r, const Density &den, const ElemOp<double> &op, Bufs<double> &b,
+                        PcgState *st, int want, cudaStream_t s, int *host_nactive, int max_iters_backstop, Mg &mg,
+                        const ApplyArgs<float> &a32, float *r32, float *z32, double *z64) {
+    const size_t N = (size_t)r * r * r;
+    double *partial = nullptr;
+    const int gv = grid1d(N, kBlk, 148 * 4);
+    const int gc = grid1d(18 * N, kBlk, 148 * 8);
+    SHL_TRY(ws_get_t(ctx, "pcg_partial", (size_t)gv * 12, &partial));
+    VecArgs<double> va{N, b.x, b.r, b.p, b.q, b.dinv, st, partial, z64};
+    // start: z = M^-1 r, p = z, rz = r.z for the wanted load cases
+    cvt_f64_f32_kernel<<<gc, kBlk, 0, s>>>(N, nullptr, b.r, r32);
+    ++ctx->launches;
+    SHL_TRY(mg_vcycle(ctx, &mg, a32, r32, z32, nullptr, s));
+    cvt_f32_f64_kernel<<<gc, kBlk, 0, s>>>(N, nullptr, z32, z64);
+    pcg_init_kernel<double><<<gv, kBlk, 0, s>>>(va, want, 0);
+    ctx->launches += 2;
+    SHL_CUDA(ctx, cudaGetLastError());
+    ApplyArgs<double> a = make_apply<double>(r, den, op);
+    a.p = b.p;
+    a.q = b.q;
+    a.pin = 1;
+    a.dot = 1;
+    a.defer = 1;  // p.q is reduced by the update kernel
+    a.st = st;
+    a.ticket = &st->ticket_apply;
+    {
+        const size_t nblk = (size_t)apply_partial_rows<double>(r, den);
+        double *ap = nullptr;
+        SHL_TRY(ws_get_t(ctx, "apply_partial", nblk * 6, &ap));
+        a.partial = ap;
+    }
+    const VecGeom vg = vec_geom<double>(N);
+    const FineJacobi fj{mg.lv[0].Dinv, mg.lv[0].omega, z32};
+    const int chunk = 8;
+    IterGraph graph;
+    SHL_TRY(capture_iteration(ctx, s, &graph, [&]() -> int {
+        SHL_TRY(launch_apply<double>(ctx, a, s));
+        launch_vec_update<double>(ctx, va, vg, fj, true, ApplyDot{a.partial, apply_partial_rows<double>(r, den)},
+                                  s);
+        pdl_launch(cvt_f64_f32_kernel, gc, kBlk, 0, s, N, (const PcgState *)st, (const double *)b.r, r32);
+        SHL_TRY(mg_vcycle(ctx, &mg, a32, r32, z32, st, s, kVcFirstFused));
+        pdl_launch(cvt_f32_f64_kernel, gc, kBlk, 0, s, N, (const PcgState *)st, (const float *)z32, z64);
+        pcg_rz_kernel<double><<<gv, kBlk, 0, s>>>(va);
+        pcg_direction_kernel<double><<<gv, kBlk, 0, s>>>(va);
+        ctx->launches += 4;
+        return SHL_OK;
+    }, "pcg64mg_" + std::to_string(r) + (den.Ev == 0.0 ? "_a" : "")));
+    const long long cap = (long long)max_iters_backstop + 2 * chunk;
+    for (long long it = 0;; it += chunk) {
+        if (it > cap) return set_err(ctx, SHL_ENOCONV, "PCG did not stop within %lld iterations", cap);
+        SHL_TRY(replay(ctx, s, &graph, chunk));
+        SHL_CUDA(ctx, cudaMemcpyAsync(host_nactive, &st->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SHL_CUDA(ctx, cudaStreamSynchronize(s));
+        if (*host_nactive == 0) break;
+    }
+    return SHL_OK;
+}
+
 // Full solve: x64 (18 N doubles, device) receives the displacements.
 inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_opts *o, double *x64, bool warm,
                      cudaStream_t s, SolveOut *out) {
@@ -1328,11 +1391,29 @@ inline int run_solve(shl_ctx *ctx, int r, const Density &den, const shl_solve_op
         ++ctx->launches;
         SHL_CUDA(ctx, cudaMemcpyAsync(st->bnorm2, norms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (warm) SHL_TRY(resid64(ctx, r, den, op64, x64, r64, 1, nullptr, s));
+        // multigrid preconditioner in FP32 (when asked and the grid coarsens far enough)
+        Mg mg;
+        const bool use_mg = (o->precond == SHL_PRECOND_MG) && mg_plan(r, &mg);
+        ElemOp<float> op32;
+        float *r32 = nullptr, *z32 = nullptr;
+        double *z64 = nullptr;
+        if (use_mg) {
+            SHL_TRY(get_op(ctx, o->nu, r, &op32));
+            SHL_TRY(ws_get_t(ctx, "r32", NV, &r32));
+            SHL_TRY(ws_get_t(ctx, "z32", NV, &z32));
+            SHL_TRY(ws_get_t(ctx, "z64", NV, &z64));
+            SHL_TRY(mg_setup(ctx, r, den, o, &mg, s));
+        }
+        const ApplyArgs<float> a32 = use_mg ? make_apply<float>(r, den, op32) : ApplyArgs<float>{};
+        out->precond = use_mg ? SHL_PRECOND_MG : SHL_PRECOND_JACOBI;
         // CG stops on its recurrence residual, which drifts from f - K x in
         // finite precision; restart from the true residual until it meets tol.
         int want = 0x3f, restarts = 0;
         for (;; ++restarts) {
-            SHL_TRY(pcg_run<double>(ctx, r, den, op64, b, st, want, 0, s, hp.nactive, maxit));
+            if (use_mg)
+                SHL_TRY(pcg_run_mg64(ctx, r, den, op64, b, st, want, s, hp.nactive, maxit, mg, a32, r32, z32, z64));
+            else
+                SHL_TRY(pcg_run<double>(ctx, r, den, op64, b, st, want, 0, s, hp.nactive, maxit));
             int its[6], nerr = 0;
             SHL_CUDA(ctx, cudaMemcpyAsync(its, st->iters, sizeof(its), cudaMemcpyDeviceToHost, s));
             SHL_CUDA(ctx, cudaMemcpyAsync(&nerr, &st->numeric_err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -144,8 +144,10 @@ def test_thin_shell_active_set_multigrid_matches_fp64(ctx, r):
     multigrid), both to a relative residual of 1e-10."""
     d = inputs.shell_256(0)
     o32 = shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP32_REFINE, active=1)
-    o64 = shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP64, active=1, max_iter=100000)
+    o64 = shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP64, active=1, max_iter=100000,
+                                 precond=shl.SHL_PRECOND_JACOBI)
     C32, s32 = shl.shl_homogenize(ctx, d, r, o32)
     C64, s64 = shl.shl_homogenize(ctx, d, r, o64)
     assert s32["status"] == 0 and s64["status"] == 0 and s32["precond"] == shl.SHL_PRECOND_MG
+    assert s64["precond"] == shl.SHL_PRECOND_JACOBI
     assert entry_err(C32, C64) <= 1e-9

@@ -209,12 +209,16 @@ def test_chom_from_given_displacements(ctx):
 # whole path
 # --------------------------------------------------------------------------- #
 
+@pytest.mark.parametrize("precond", [shl.SHL_PRECOND_MG, shl.SHL_PRECOND_JACOBI])
 @pytest.mark.parametrize("name,seed", [("plain32_s0", 0), ("plain32_s1", 1)])
-def test_homogenize_fp64_matches_oracle(ctx, name, seed):
+def test_homogenize_fp64_matches_oracle(ctx, name, seed, precond):
+    """The FP64 mode (config 1) with either preconditioner: FP64 CG with the
+    FP32 multigrid V-cycle, and plain point-Jacobi PCG."""
     g = gold(name)
     d = inputs.plain_32(seed)
-    C, st = shl.shl_homogenize(ctx, d, 32, shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP64))
-    assert st["status"] == 0 and st["n_ambiguous"] == 0
+    C, st = shl.shl_homogenize(ctx, d, 32, shl.default_solve_opts(tol=1e-10, precision=shl.SHL_FP64,
+                                                                   precond=precond))
+    assert st["status"] == 0 and st["n_ambiguous"] == 0 and st["precond"] == precond
     assert st["n_solid"] == g["n_solid"]
     assert max(st["relres"]) <= 1e-10
     assert np.abs(C - C.T).max() <= 1e-14 * np.abs(C).max()
