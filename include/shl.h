@@ -129,7 +129,8 @@ typedef struct {
  *   mg_nu          smoothing sweeps before and after the coarse correction on
  *                  the fine level and the first coarse level (<= 0: 1)
  *   mg_nu_coarse   the same on the smaller levels (index >= 2, at most 1/64 of
- *                  the fine nodes), whose sweeps are cheap (<= 0: 3)
+ *                  the fine nodes), whose sweeps are cheap (<= 0: 2 for
+ *                  r <= 32, else 3)
  *   mg_gamma       visits of each level >= 2 per visit of the level above: 1
  *                  V-cycle, 2 W-cycle; 0 (default) W-cycle from r = 128 up,
  *                  where those levels cost little next to the fine level
